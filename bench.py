@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark: exact top-k sparse-vector KNN join on GB300.
+
+Workload (default): the spectrum-shaped plain join -- |R| = 100,000 query vectors
+(nnz log-normal, mean ~150, [20, 600]), |S| = 2,000,000 database vectors (nnz
+U{20..60}), d = 10,000, ids from a shared 8-component Gaussian mixture, uint8
+intensities 1..100, int32 scores, k = 5; seeded synthetic data.
+
+One step = one knn_join call over all of R (validation of R done once beforehand;
+the index of S is built once and its build time is reported separately).
+Multi-GPU: one process per GPU, each joins its own 100,000 rows against a replica of
+the index (R rows are independent: weak scaling, no collective on the data path).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "R rows joined/sec (exact top-k) + posting GB/s vs HBM peak; learned/batched vs plain"
+UNIT = "rows/s"
+L2_BYTES = 129e6
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["iiib", "iib"], default="iiib")
+    ap.add_argument("--n-r", type=int, default=100000)
+    ap.add_argument("--n-s", type=int, default=2000000)
+    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--block-size", type=int, default=0)
+    ap.add_argument("--n-levels", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-oracle sample time")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload(args, rank):
+    from paper_1011_2807_gb300 import synth
+    S = synth.spectrum_u8(args.n_s, synth.config_seed(2, "S"), role="S")
+    R = synth.spectrum_u8(args.n_r, synth.config_seed(2, "R") + 7919 * rank, role="R")
+    return R, S
+
+
+def workload_name(args):
+    return (f"spectrum-shaped plain join: |R|={args.n_r:,} (nnz lognormal mean 150, [20,600]), "
+            f"|S|={args.n_s:,} (nnz U[20,60]), d=10,000, Gaussian-mixture ids, uint8 1..100, "
+            f"int32 scores, k={args.k}")
+
+
+def iib_postings(R, S):
+    """eq. 4 second term: postings an unrefined IIB scan touches."""
+    df = np.bincount(S.indices, minlength=S.dim).astype(np.int64)
+    return int(df[R.indices].sum())
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(kernel_src):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this
+    kernel source (sha256 recorded in the summary); else None."""
+    path = os.path.join(ROOT, "profiles", "k_join_spectrum_config2.md")
+    if not os.path.exists(path):
+        return None, None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"join_cu_sha256:\s*([0-9a-f]{64})", txt)
+    if not m or not h:
+        return None, None
+    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    if cur != h.group(1):
+        return None, "kernel changed since the ncu capture"
+    return float(m.group(1)), None
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_oracle_rows_per_s(R, S, k, target_s, rows_lo=256, rows_hi=65536):
+    """The CPU oracle (Algorithm 3 in the block nested loop, all host cores) on a
+    bounded sample of R rows against the full S; returns (rows/s, rows, seconds)."""
+    import oracle
+    oracle.build()
+    n0 = min(rows_lo, R.n_rows)
+    t = time.perf_counter()
+    oracle.iib_join(R.slice_rows(0, n0), S, k, threads=0)
+    t0 = time.perf_counter() - t
+    n = int(min(rows_hi, R.n_rows, max(n0, n0 * target_s / max(t0, 1e-3))))
+    if n <= n0:
+        return n0 / t0, n0, t0
+    t = time.perf_counter()
+    oracle.iib_join(R.slice_rows(0, n), S, k, threads=0)
+    dt = time.perf_counter() - t
+    return n / dt, n, dt
+
+
+# ----------------------------------------------------------------------------------
+# reference arm: the CPU oracle, timed on the host cores
+# ----------------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    R, S = workload(args, 0)
+    cores = os.cpu_count() or 1
+    # one step = the oracle on a bounded sample of rows (rotating through R)
+    rows_per_step = 1024
+    total_rows, total_t = 0, 0.0
+    for i in range(args.warmup + args.steps):
+        a = (i * rows_per_step) % max(1, R.n_rows - rows_per_step)
+        Rs = R.slice_rows(a, min(R.n_rows, a + rows_per_step))
+        t = time.perf_counter()
+        oracle.iib_join(Rs, S, args.k, threads=0)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            total_rows += Rs.n_rows
+            total_t += dt
+    v = total_rows / total_t
+    sample = (f"{rows_per_step} R rows per step against all {S.n_rows:,} S vectors "
+              f"(CPU oracle: Algorithm 3 in the block nested loop, OpenMP over rows)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(args), "k": args.k},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import paper_1011_2807_gb300 as knn
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    R, S = workload(args, rank)
+    k = args.k
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    idx = knn.knn_join_build_index(S, block_size=args.block_size, n_levels=args.n_levels)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t
+    info = idx.info()
+
+    Rd = knn.DeviceCSR.from_host(R)
+    ids = torch.empty((R.n_rows, k), dtype=torch.int32, device="cuda")
+    sc = torch.empty((R.n_rows, k), dtype=torch.int32, device="cuda")
+    kw = dict(mode=args.mode, threads=args.threads, out_ids=ids, out_scores=sc)
+    # validate R once, and count the postings one step scans
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    knn.knn_join(idx, Rd, k, postings_scanned=cnt, **kw)
+    torch.cuda.synchronize()
+    scanned = int(cnt.item())
+    p_iib = iib_postings(R, S)
+
+    for _ in range(args.warmup):
+        knn.knn_join(idx, Rd, k, skip_validation=True, **kw)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    launches0 = knn.knn_kernel_launch_count()
+    ev0.record(stream)
+    for i in range(args.steps):
+        step_ev[i][0].record(stream)
+        knn.knn_join(idx, Rd, k, skip_validation=True, **kw)
+        step_ev[i][1].record(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = knn.knn_kernel_launch_count() - launches0
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    rows_total = R.n_rows * world * args.steps
+    value = rows_total / (ms / 1000.0)
+
+    # end to end through the public call with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        Rh_t = [pin(R.indptr), pin(R.indices), pin(R.values)]
+        from paper_1011_2807_gb300 import synth
+        Rh = synth.CSR(Rh_t[0].numpy(), Rh_t[1].numpy(), Rh_t[2].numpy(), R.dim)
+        hid = torch.empty((R.n_rows, k), dtype=torch.int32, pin_memory=True)
+        hsc = torch.empty((R.n_rows, k), dtype=torch.int32, pin_memory=True)
+        for _ in range(max(1, args.warmup)):
+            knn.knn_join(idx, Rh, k, mode=args.mode, threads=args.threads, out_ids=hid, out_scores=hsc,
+                         outputs_on_host=True)
+        barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            knn.knn_join(idx, Rh, k, mode=args.mode, threads=args.threads, out_ids=hid, out_scores=hsc,
+                         outputs_on_host=True)
+        dt = time.perf_counter() - t
+        if world > 1:
+            tt = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        h2d = int(R.indptr.nbytes + R.indices.nbytes + R.values.nbytes)
+        d2h = int(hid.numel() * 4 + hsc.numel() * 4)
+        e2e = {"value": R.n_rows * world * args.steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "validation": "R validated on every call"}
+        # results of the two paths agree
+        assert torch.equal(hid, ids.cpu()) and torch.equal(hsc, sc.cpu())
+
+    # roofline of the dominant kernel (the join; index build excluded)
+    peak, peak_src = measured_peak()
+    bytes_post = 4 * scanned
+    bytes_r = R.indices.nbytes + R.values.nbytes + R.indptr.nbytes
+    bytes_out = R.n_rows * k * 8
+    alg_bytes = bytes_post + bytes_r + bytes_out
+    kern_ms = statistics.mean(step_ms)
+    achieved = alg_bytes / (kern_ms / 1000.0) / 1e9
+    traffic, traffic_note = profiled_traffic(os.path.join(ROOT, "paper_1011_2807_gb300", "csrc", "join.cu"))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_join (posting scan + accumulate + select + top-k, fused)",
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "bytes_per_unit": "4 B per posting scanned + 5 B per R feature + 8 B per R row index + 8k B output",
+                "iib_equivalent_GBps": (4 * p_iib + bytes_r + bytes_out) / (kern_ms / 1000.0) / 1e9}
+    if traffic_note:
+        roofline["traffic_note"] = traffic_note
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n, dt = cpu_oracle_rows_per_s(R, S, k, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"first {n:,} of the {R.n_rows:,} R rows against all {S.n_rows:,} S vectors, "
+                         f"{dt:.1f} s (Algorithm 3 in the block nested loop, OpenMP over rows, "
+                         f"index build included)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": workload_name(args), "n_r_per_gpu": R.n_rows, "n_s": S.n_rows,
+                           "dim": S.dim, "k": k, "mode": args.mode, "block_size": info["block_size"],
+                           "n_blocks": info["n_blocks"], "n_levels": info["n_levels"],
+                           "index_device_bytes": info["device_bytes"], "index_build_s": build_s,
+                           "l2": f"inputs larger than L2 (index {info['device_bytes'] / 1e9:.2f} GB "
+                                 f"> 129 MB L2); no flush",
+                           "postings_scanned_per_step": scanned, "postings_iib_eq4_per_step": p_iib,
+                           "timed_calls": "knn_join on device-resident R, validated once before timing",
+                           "parallelism": f"R rows split over {world} GPU(s), index replicated"},
+                "gpu_launches": launches, "roofline": roofline, "clocks": clk,
+                "e2e": e2e, "cpu_baseline": cpu,
+                "kernel_ms_per_step": kern_ms}
+        print(json.dumps(line), flush=True)
+    idx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

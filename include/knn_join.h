@@ -1,0 +1,180 @@
+/*
+ * knn_join.h -- C ABI of the GB300 sparse-vector KNN join library (libknnjoin.so).
+ *
+ * Paper: Wang, Lin, Huang, Wang, He, "Efficient K-Nearest Neighbor Join Algorithms
+ * for High Dimensional Sparse Data".
+ *
+ * Problem (Section 3): for every vector r of R, return the k vectors s of S with the
+ * largest dot(r, s) = sum_d r[d] * s[d] (eq. 1).  A sparse vector is a set of
+ * features (d, w) with w > 0 in ascending d (Section 3).  This library orders equal
+ * scores by ascending S id, leaves out zero scores, and pads a row that has fewer
+ * than k positive scores with id -1 and score 0.
+ *
+ * Method: the inverted index of S (Section 4.3, Algorithm 3) split into S blocks, with
+ * the threshold-based refinement of Section 4.4 (Algorithm 4): each list is ordered
+ * so that the postings the refinement indexes come first, and a running k-th score
+ * per query row (the row's pruneScore, which bounds MinPruneScore from below for a
+ * one-row R block) picks how much of each list is scanned.  Scores of the vectors
+ * found this way are completed with their unindexed features (Algorithm 4,
+ * Find_Matches_IIIB) and a per-row top-k keeps the result.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a knn_status; nothing is thrown or aborted across the ABI.
+ *     On failure knn_last_error() returns a message for the calling thread.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is queued
+ *     on it; calls that must read a result back on the host (sizes, validation
+ *     flags) synchronise that stream, and say so.
+ *   - Pointers flagged on_device are device pointers of the current CUDA device;
+ *     otherwise they are host pointers (pinned or pageable).
+ *   - Input arrays are owned by the caller and only read.  Output arrays are owned
+ *     by the caller and must hold the stated number of elements.
+ *   - Device memory the library needs for itself (an index, scratch) comes from the
+ *     allocator installed with knn_set_allocator (default: cudaMallocAsync /
+ *     cudaFreeAsync on the call's stream).
+ */
+#ifndef KNN_JOIN_H
+#define KNN_JOIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KNN_OK = 0,
+    KNN_EINVAL = 1,        /* an argument or an input vector breaks the rules above      */
+    KNN_ENOMEM = 2,        /* the allocator returned NULL                                 */
+    KNN_ECUDA = 3,         /* a CUDA runtime call failed (message in knn_last_error)      */
+    KNN_ETIMEOUT = 4,      /* a bounded device-side wait gave up                          */
+    KNN_EUNSUPPORTED = 5   /* valid input outside this build's limits (k, row size, ...)  */
+} knn_status;
+
+typedef enum {
+    KNN_U8 = 0,   /* uint8 weights, int32 scores (exact)                                  */
+    KNN_F32 = 1   /* float32 weights, float32 scores                                      */
+} knn_dtype;
+
+/* A set of sparse vectors in CSR form.
+ *   indptr  int64[n_rows + 1], indptr[0] == 0, non-decreasing
+ *   indices int32[indptr[n_rows]], 0 <= d < dim, strictly ascending within a row
+ *   values  uint8 or float32 [indptr[n_rows]], every w > 0 (and finite)
+ * Rows may be empty.  Section 3 fixes w > 0; the Section 4.4 bound needs w >= 0.   */
+typedef struct {
+    int64_t n_rows;
+    int32_t dim;
+    knn_dtype dtype;
+    const int64_t* indptr;
+    const int32_t* indices;
+    const void* values;
+    int32_t on_device;     /* 1: the three arrays are device pointers; 0: host pointers */
+} knn_csr;
+
+/* Limits of this build. */
+#define KNN_MAX_K 64              /* largest k of knn_join                               */
+#define KNN_MAX_LEVELS 32         /* largest number of threshold levels of an index      */
+#define KNN_MAX_BLOCK 32768       /* largest S block (S vectors per block)               */
+
+/* Allocator used for every device buffer the library owns.  `alloc` returns a device
+ * pointer of at least `bytes` bytes usable on `stream`, or NULL; `release` gives it
+ * back.  Passing NULL for both restores the default (cudaMallocAsync/cudaFreeAsync).
+ * Process-wide; install it before building an index.                              */
+typedef void* (*knn_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*knn_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+knn_status knn_set_allocator(knn_alloc_fn alloc, knn_free_fn release, void* ctx);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* knn_last_error(void);
+
+/* Library version string. */
+const char* knn_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far. */
+int64_t knn_kernel_launch_count(void);
+
+/* ------------------------------------------------------------------------------ */
+/* Index of S (Section 4.3 inverted lists, Algorithm 3's Create_Inverted_List_IIB,  */
+/* with Section 4.4's index cut precomputed for a ladder of thresholds)             */
+/* ------------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t block_size;   /* S vectors per S block: power of two in [256, 32768];
+                             0 = 16384 (or the next power of two >= |S| if smaller)   */
+    int32_t n_levels;     /* threshold levels of the Section 4.4 cut, 1..32; 0 = 16;
+                             1 = no refinement (every list scanned whole, IIB)       */
+} knn_build_opts;
+
+typedef struct knn_index knn_index;
+
+typedef struct {
+    int64_t n_rows, nnz;
+    int32_t dim, block_size, n_blocks, n_levels;
+    knn_dtype dtype;
+    int32_t max_row_nnz;
+    size_t device_bytes;  /* bytes the index holds on the device */
+} knn_index_info;
+
+/* Builds the index of S on the current device.
+ *   S      the database vectors (host or device CSR, see knn_csr).
+ *   opts   NULL for defaults.
+ *   out    receives the handle; the handle owns a device copy of everything it needs
+ *          (S may be freed after the call returns).
+ * Dimension order for the Section 4.4 cut: descending document frequency in S, ties
+ * by ascending dimension.  Synchronises `stream` (validation and sizing).
+ * Errors: KNN_EINVAL for a malformed S (unsorted or repeated d, d out of range,
+ * w <= 0, bad indptr), KNN_EUNSUPPORTED for more than 2^31-1 features,
+ * KNN_ENOMEM, KNN_ECUDA.                                                           */
+knn_status knn_join_build_index(const knn_csr* S, const knn_build_opts* opts, void* stream,
+                                knn_index** out);
+
+knn_status knn_index_get_info(const knn_index* index, knn_index_info* info);
+
+/* Frees the index (its device buffers go back to the allocator on its build stream). */
+void knn_index_destroy(knn_index* index);
+
+/* ------------------------------------------------------------------------------ */
+/* Join (Algorithm 1's loop over S blocks per R row; Find_Matches of Algorithms 3/4) */
+/* ------------------------------------------------------------------------------ */
+
+typedef enum {
+    KNN_MODE_IIIB = 0,    /* threshold-refined scan (Section 4.4), the default        */
+    KNN_MODE_IIB = 1      /* every list scanned whole (Section 4.3)                   */
+} knn_mode;
+
+typedef struct {
+    knn_mode mode;
+    int32_t threads;            /* threads per CTA (128..1024, multiple of 32); 0 = auto */
+    int32_t s_groups;           /* S-block groups scanned in parallel per row; 0 = auto  */
+    const float* init_threshold;/* device float[n_rows] or NULL.  When given, row i keeps
+                                   only vectors with score >= init_threshold[i] (a
+                                   learned start for pruneScore).  NULL = 0 (strict >).  */
+    int32_t* n_found;           /* device int32[n_rows] or NULL: entries returned per row
+                                   (== k means the row's top-k is exact)                  */
+    int64_t* postings_scanned;  /* device int64[1] or NULL: postings read, added to it   */
+    int32_t outputs_on_host;    /* 1: out_ids/out_scores are host pointers; the call then
+                                   synchronises `stream` before returning                */
+    int32_t skip_validation;    /* 1: trust R (sorted, in range, w > 0)                   */
+} knn_join_opts;
+
+/* Exact top-k of every row of R against the indexed S.
+ *   index       built by knn_join_build_index (same dim and dtype as R).
+ *   R           query vectors (host or device CSR).
+ *   k           1..KNN_MAX_K.
+ *   out_ids     int32[n_rows * k]: S ids, row-major, best first, -1 padding.
+ *   out_scores  int32 (KNN_U8) or float (KNN_F32) [n_rows * k], 0 padding.
+ * Row i lists min(k, #{s : dot(r_i, s) > 0}) entries (with init_threshold: those with
+ * dot >= init_threshold[i]) ordered by (score desc, id asc).
+ * Synchronises `stream` unless skip_validation is set and R is on the device.
+ * Errors: KNN_EINVAL (bad R, dim/dtype mismatch, k < 1), KNN_EUNSUPPORTED (k > 64,
+ * a row too long for one CTA's shared memory, u8 scores that could overflow int32),
+ * KNN_ENOMEM, KNN_ECUDA.                                                           */
+knn_status knn_join(const knn_index* index, const knn_csr* R, int32_t k,
+                    const knn_join_opts* opts, int32_t* out_ids, void* out_scores,
+                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNN_JOIN_H */

@@ -1,0 +1,7 @@
+"""GB300 sparse-vector KNN join (inverted-index join with threshold refinement).
+
+The compute path is the CUDA library ``libknnjoin.so`` (C ABI in include/knn_join.h);
+:mod:`.binding` marshals arguments to it.  :mod:`.synth` draws seeded inputs.
+"""
+from .binding import (DeviceCSR, Index, KnnError, knn_join, knn_join_build_index,  # noqa: F401
+                      knn_kernel_launch_count, knn_last_error, knn_version, lib)

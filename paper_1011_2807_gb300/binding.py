@@ -1,0 +1,266 @@
+"""Thin ctypes binding of libknnjoin.so (include/knn_join.h).
+
+Marshalling only: every step of the join runs in the library's CUDA kernels.  The
+names match the C entry points.  PyTorch provides device memory (outputs, and the
+library's own buffers through the allocator hook) and streams.
+
+A CSR argument is either a host CSR (numpy ``indptr``/``indices``/``values``, e.g.
+:class:`paper_1011_2807_gb300.synth.CSR`) or a :class:`DeviceCSR` of CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libknnjoin.so")
+
+KNN_OK, KNN_EINVAL, KNN_ENOMEM, KNN_ECUDA, KNN_ETIMEOUT, KNN_EUNSUPPORTED = range(6)
+KNN_U8, KNN_F32 = 0, 1
+KNN_MODE_IIIB, KNN_MODE_IIB = 0, 1
+KNN_MAX_K = 64
+
+
+class KnnError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"knn status {status}: {message}")
+        self.status = status
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("dim", ctypes.c_int32), ("dtype", ctypes.c_int),
+                ("indptr", ctypes.c_void_p), ("indices", ctypes.c_void_p),
+                ("values", ctypes.c_void_p), ("on_device", ctypes.c_int32)]
+
+
+class _BuildOpts(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_int32), ("n_levels", ctypes.c_int32)]
+
+
+class _IndexInfo(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("nnz", ctypes.c_int64), ("dim", ctypes.c_int32),
+                ("block_size", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("dtype", ctypes.c_int),
+                ("max_row_nnz", ctypes.c_int32), ("device_bytes", ctypes.c_size_t)]
+
+
+class _JoinOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("threads", ctypes.c_int32), ("s_groups", ctypes.c_int32),
+                ("init_threshold", ctypes.c_void_p), ("n_found", ctypes.c_void_p),
+                ("postings_scanned", ctypes.c_void_p), ("outputs_on_host", ctypes.c_int32),
+                ("skip_validation", ctypes.c_int32)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+_alloc_cbs = None
+
+
+def _torch_alloc(nbytes, stream, ctx):
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:
+        return None
+
+
+def _torch_free(ptr, nbytes, stream, ctx):
+    torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def lib():
+    """Loads libknnjoin.so; raises if it was not built (there is no CPU fallback)."""
+    global _lib, _alloc_cbs
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        L.knn_last_error.restype = ctypes.c_char_p
+        L.knn_version.restype = ctypes.c_char_p
+        L.knn_kernel_launch_count.restype = ctypes.c_int64
+        L.knn_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, ctypes.c_void_p]
+        L.knn_join_build_index.argtypes = [P(_Csr), P(_BuildOpts), ctypes.c_void_p, P(ctypes.c_void_p)]
+        L.knn_index_get_info.argtypes = [ctypes.c_void_p, P(_IndexInfo)]
+        L.knn_index_destroy.argtypes = [ctypes.c_void_p]
+        L.knn_index_destroy.restype = None
+        L.knn_join.argtypes = [ctypes.c_void_p, P(_Csr), ctypes.c_int32, P(_JoinOpts),
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        _alloc_cbs = (_ALLOC_FN(_torch_alloc), _FREE_FN(_torch_free))
+        _check(L, L.knn_set_allocator(_alloc_cbs[0], _alloc_cbs[1], None))
+        _lib = L
+        return L
+
+
+def _check(L, status):
+    if status != KNN_OK:
+        raise KnnError(status, L.knn_last_error().decode())
+
+
+def knn_last_error() -> str:
+    return lib().knn_last_error().decode()
+
+
+def knn_version() -> str:
+    return lib().knn_version().decode()
+
+
+def knn_kernel_launch_count() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(lib().knn_kernel_launch_count())
+
+
+# ----------------------------------------------------------------------------------
+# CSR marshalling
+# ----------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class DeviceCSR:
+    """CSR held in CUDA tensors (int64 indptr, int32 indices, uint8/float32 values)."""
+
+    indptr: torch.Tensor
+    indices: torch.Tensor
+    values: torch.Tensor
+    dim: int
+
+    @property
+    def n_rows(self) -> int:
+        return int(self.indptr.shape[0] - 1)
+
+    @staticmethod
+    def from_host(x, device="cuda") -> "DeviceCSR":
+        return DeviceCSR(torch.from_numpy(np.ascontiguousarray(x.indptr, np.int64)).to(device),
+                         torch.from_numpy(np.ascontiguousarray(x.indices, np.int32)).to(device),
+                         torch.from_numpy(np.ascontiguousarray(x.values)).to(device), int(x.dim))
+
+
+def _dtype_code(vdtype) -> int:
+    if vdtype in (np.uint8, torch.uint8):
+        return KNN_U8
+    if vdtype in (np.float32, torch.float32):
+        return KNN_F32
+    raise TypeError(f"values must be uint8 or float32, got {vdtype}")
+
+
+def _csr(x, keep: list) -> _Csr:
+    if isinstance(x, DeviceCSR):
+        for t, dt in ((x.indptr, torch.int64), (x.indices, torch.int32)):
+            if t.dtype != dt or not t.is_contiguous():
+                raise TypeError("DeviceCSR needs contiguous int64 indptr and int32 indices")
+        if not x.values.is_contiguous():
+            raise TypeError("values must be contiguous")
+        on_dev = int(x.indptr.is_cuda)
+        keep.append(x)
+        return _Csr(x.n_rows, int(x.dim), _dtype_code(x.values.dtype), x.indptr.data_ptr(),
+                    x.indices.data_ptr(), x.values.data_ptr(), on_dev)
+    indptr = np.ascontiguousarray(x.indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(x.indices, dtype=np.int32)
+    values = np.ascontiguousarray(x.values)
+    keep.extend([indptr, indices, values])
+    return _Csr(indptr.shape[0] - 1, int(x.dim), _dtype_code(values.dtype), indptr.ctypes.data,
+                indices.ctypes.data, values.ctypes.data, 0)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+# ----------------------------------------------------------------------------------
+# index
+# ----------------------------------------------------------------------------------
+
+class Index:
+    """Owns a knn_index handle (freed on close() or garbage collection)."""
+
+    def __init__(self, handle: int, dtype: int):
+        self._h = handle
+        self.dtype = dtype
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("index is closed")
+        return self._h
+
+    def info(self) -> dict:
+        inf = _IndexInfo()
+        L = lib()
+        _check(L, L.knn_index_get_info(self.handle, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in _IndexInfo._fields_}
+
+    def close(self):
+        if self._h:
+            lib().knn_index_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def knn_join_build_index(S, block_size: int = 0, n_levels: int = 0, stream=None) -> Index:
+    """Builds the index of S (see include/knn_join.h)."""
+    L = lib()
+    keep = []
+    c = _csr(S, keep)
+    opts = _BuildOpts(int(block_size), int(n_levels))
+    h = ctypes.c_void_p()
+    _check(L, L.knn_join_build_index(ctypes.byref(c), ctypes.byref(opts), _stream_ptr(stream),
+                                     ctypes.byref(h)))
+    return Index(h.value, c.dtype)
+
+
+# ----------------------------------------------------------------------------------
+# join
+# ----------------------------------------------------------------------------------
+
+def knn_join(index: Index, R, k: int, *, mode: str = "iiib", threads: int = 0, s_groups: int = 0,
+             init_threshold: torch.Tensor | None = None, n_found: torch.Tensor | None = None,
+             postings_scanned: torch.Tensor | None = None, out_ids=None, out_scores=None,
+             outputs_on_host: bool = False, skip_validation: bool = False, stream=None):
+    """Exact top-k of every row of R; returns (ids, scores).
+
+    Device outputs are torch tensors on the current device unless ``out_ids`` /
+    ``out_scores`` are given.  With ``outputs_on_host`` the outputs are pinned CPU
+    tensors (or numpy arrays) filled by the library's device-to-host copies.
+    """
+    L = lib()
+    keep = []
+    c = _csr(R, keep)
+    n = c.n_rows
+    sdt = torch.int32 if index.dtype == KNN_U8 else torch.float32
+    if out_ids is None:
+        if outputs_on_host:
+            out_ids = torch.empty((n, k), dtype=torch.int32, pin_memory=True)
+            out_scores = torch.empty((n, k), dtype=sdt, pin_memory=True)
+        else:
+            out_ids = torch.empty((n, k), dtype=torch.int32, device="cuda")
+            out_scores = torch.empty((n, k), dtype=sdt, device="cuda")
+    opts = _JoinOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), int(s_groups),
+                     _ptr(init_threshold), _ptr(n_found), _ptr(postings_scanned),
+                     int(bool(outputs_on_host)), int(bool(skip_validation)))
+    ip = out_ids.ctypes.data if isinstance(out_ids, np.ndarray) else out_ids.data_ptr()
+    sp = out_scores.ctypes.data if isinstance(out_scores, np.ndarray) else out_scores.data_ptr()
+    _check(L, L.knn_join(index.handle, ctypes.byref(c), int(k), ctypes.byref(opts), ip, sp,
+                         _stream_ptr(stream)))
+    return out_ids, out_scores

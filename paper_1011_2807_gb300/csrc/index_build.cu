@@ -1,0 +1,359 @@
+// Index build: the inverted lists of S (Section 4.3, Create_Inverted_List_IIB of
+// Algorithm 3), split into S blocks, with the threshold cut of Section 4.4
+// (Create_Inverted_List_IIIB of Algorithm 4) precomputed for a ladder of thresholds.
+//
+// Algorithm 4 walks the features of s in a dimension order, adds maxWeight_d * w to a
+// bound t, and indexes the features from the one where t exceeds MinPruneScore on.
+// The index is built before any R is known, so this build
+//   * fixes one dimension order pi for all queries (descending document frequency in
+//     S, ties by ascending d; Theorem 1 holds for any order),
+//   * keeps the R-dependent factor out of the bound: with M >= every weight of the
+//     query, t(j) <= M * tS(j), where tS(j) is the sum of s's weights over its first
+//     j+1 features in pi order,
+//   * precomputes, for each level value L_l of a ladder (L_0 = 0 < L_1 < ...), which
+//     features a query whose threshold theta satisfies M * L_l < theta may leave
+//     unindexed: exactly those with tS(j) <= L_l (a prefix of s in pi order).
+// A posting's bucket is the highest level at which it is still indexed,
+// max{l : tS(j) > L_l}.  Each (S block, d) list is stored bucket-descending, so the
+// part of the list indexed at level l is a prefix, and binoff gives its end.
+//
+// Layout in HBM (all device arrays owned by the index):
+//   binoff   u32 [n_blocks * dim * n_levels + 1]: bin (b, d, n_levels-1-bucket) start
+//   postings u32 (lid | w << 16) for uint8, uint2 {lid, float bits} for float32
+//   s_indptr / sp_d / sp_w: S in CSR with each row's features in pi order
+//   n_unidx  u16 [n_levels][|S|]: unindexed prefix length of s at level l
+//   ubound   u32 [n_levels][|S|]: tS of that prefix (u32 for uint8, float bits rounded up)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace knn {
+
+__global__ void k_df(const int32_t* __restrict__ idx, int64_t nnz, uint32_t* __restrict__ df) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < nnz; i += stride) atomicAdd(&df[idx[i]], 1u);
+}
+
+// rank[d] = number of dimensions ahead of d in (df desc, d asc) order
+__global__ void k_rank(const uint32_t* __restrict__ df, int32_t dim, int32_t* __restrict__ rank) {
+    __shared__ uint32_t tile[1024];
+    int32_t d = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t f = d < dim ? df[d] : 0u;
+    int32_t r = 0;
+    for (int32_t t0 = 0; t0 < dim; t0 += 1024) {
+        __syncthreads();
+        for (int32_t i = threadIdx.x; i < 1024; i += blockDim.x)
+            tile[i] = t0 + i < dim ? df[t0 + i] : 0u;
+        __syncthreads();
+        int32_t lim = min(1024, dim - t0);
+        for (int32_t i = 0; i < lim; i++) {
+            uint32_t g = tile[i];
+            int32_t e = t0 + i;
+            r += (g > f) || (g == f && e < d);
+        }
+    }
+    if (d < dim) rank[d] = r;
+}
+
+template <class W>
+struct WTraits;
+template <>
+struct WTraits<uint8_t> {
+    using Sum = uint32_t;
+    __device__ static uint32_t bound_bits(uint32_t t) { return t; }
+};
+template <>
+struct WTraits<float> {
+    using Sum = double;
+    // float not below the double value (the bound must not shrink)
+    __device__ static uint32_t bound_bits(double t) {
+        float f = __double2float_ru(t);
+        return __float_as_uint(f);
+    }
+};
+
+struct CutParams {
+    int64_t n_rows;
+    int32_t n_levels;
+    float levels[KNN_MAX_LEVELS];
+};
+
+// one warp per s: pi-order the features, prefix sums tS, buckets, per-level prefix data
+template <class W>
+__global__ void k_cut_order(const int64_t* __restrict__ indptr, const int32_t* __restrict__ idx,
+                            const W* __restrict__ val, const int32_t* __restrict__ rank,
+                            CutParams p, int32_t* __restrict__ sp_d, W* __restrict__ sp_w,
+                            uint8_t* __restrict__ bucket, uint16_t* __restrict__ n_unidx,
+                            uint32_t* __restrict__ ubound) {
+    using Sum = typename WTraits<W>::Sum;
+    const int lane = threadIdx.x & 31;
+    int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
+    for (; s < p.n_rows; s += nwarps) {
+        const int64_t a = indptr[s], b = indptr[s + 1];
+        const int32_t n = (int32_t)(b - a);
+        // position of feature j in pi order = number of features of s ranked before it
+        for (int32_t j = lane; j < n; j += 32) {
+            int32_t rj = rank[idx[a + j]];
+            int32_t pos = 0;
+            for (int32_t q = 0; q < n; q++) pos += rank[idx[a + q]] < rj;
+            sp_d[a + pos] = idx[a + j];
+            sp_w[a + pos] = val[a + j];
+        }
+        __threadfence_block();
+        __syncwarp();
+        Sum carry = 0;
+        uint32_t my_n = 0;      // lane l keeps level l's unindexed count
+        Sum my_u = 0;           // ... and its prefix sum
+        for (int32_t c = 0; c < n; c += 32) {
+            int32_t j = c + lane;
+            bool valid = j < n;
+            Sum x = valid ? (Sum)sp_w[a + j] : (Sum)0;
+            // inclusive warp scan
+            for (int o = 1; o < 32; o <<= 1) {
+                Sum y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            Sum ts = carry + x;
+            carry = __shfl_sync(0xffffffffu, ts, 31);
+            int bk = 0;
+            for (int l = 1; l < p.n_levels; l++) {
+                bool un = valid && (double)ts <= (double)p.levels[l];
+                bk += (valid && !un) ? 1 : 0;
+                unsigned m = __ballot_sync(0xffffffffu, un);
+                int hi = m ? 31 - __clz(m) : 0;
+                Sum top = __shfl_sync(0xffffffffu, ts, hi);
+                if (lane == l && m) {
+                    my_n += __popc(m);
+                    my_u = top;
+                }
+            }
+            if (valid) bucket[a + j] = (uint8_t)bk;
+        }
+        if (lane < p.n_levels) {
+            n_unidx[(int64_t)lane * p.n_rows + s] = (uint16_t)min(my_n, 65535u);
+            ubound[(int64_t)lane * p.n_rows + s] = WTraits<W>::bound_bits(my_u);
+        }
+    }
+}
+
+struct BinParams {
+    int64_t n_rows;
+    int32_t dim, n_levels, block_shift;
+};
+
+__device__ inline size_t bin_of(const BinParams& p, int64_t s, int32_t d, int bk) {
+    size_t blk = (size_t)(s >> p.block_shift);
+    return ((blk * (size_t)p.dim + (size_t)d) * (size_t)p.n_levels) + (size_t)(p.n_levels - 1 - bk);
+}
+
+__global__ void k_bin_count(const int64_t* __restrict__ indptr, const int32_t* __restrict__ sp_d,
+                            const uint8_t* __restrict__ bucket, BinParams p, uint32_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
+    for (; s < p.n_rows; s += nwarps) {
+        for (int64_t j = indptr[s] + lane; j < indptr[s + 1]; j += 32)
+            atomicAdd(&cnt[bin_of(p, s, sp_d[j], bucket[j])], 1u);
+    }
+}
+
+template <class W>
+__global__ void k_scatter(const int64_t* __restrict__ indptr, const int32_t* __restrict__ sp_d,
+                          const W* __restrict__ sp_w, const uint8_t* __restrict__ bucket, BinParams p,
+                          uint32_t* __restrict__ cursor, void* __restrict__ postings) {
+    const int lane = threadIdx.x & 31;
+    int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
+    const uint32_t lid_mask = (1u << p.block_shift) - 1u;
+    for (; s < p.n_rows; s += nwarps) {
+        uint32_t lid = (uint32_t)s & lid_mask;
+        for (int64_t j = indptr[s] + lane; j < indptr[s + 1]; j += 32) {
+            uint32_t pos = atomicAdd(&cursor[bin_of(p, s, sp_d[j], bucket[j])], 1u);
+            W w = sp_w[j];
+            if constexpr (sizeof(W) == 1) {
+                ((uint32_t*)postings)[pos] = lid | ((uint32_t)w << 16);
+            } else {
+                ((uint2*)postings)[pos] = make_uint2(lid, __float_as_uint((float)w));
+            }
+        }
+    }
+}
+
+static int ilog2(int64_t v) {
+    int r = 0;
+    while ((int64_t(1) << r) < v) r++;
+    return r;
+}
+
+}  // namespace knn
+
+using namespace knn;
+
+extern "C" knn_status knn_join_build_index(const knn_csr* S, const knn_build_opts* opts, void* stream_,
+                                           knn_index** out) {
+    if (!out) return fail(KNN_EINVAL, "out is NULL");
+    *out = nullptr;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    knn_build_opts o = {};
+    if (opts) o = *opts;
+    int32_t nl = o.n_levels == 0 ? 16 : o.n_levels;
+    if (nl < 1 || nl > KNN_MAX_LEVELS) return fail(KNN_EINVAL, "n_levels must be in [1, %d]", KNN_MAX_LEVELS);
+    if (o.block_size != 0) {
+        if (o.block_size < 256 || o.block_size > KNN_MAX_BLOCK || (o.block_size & (o.block_size - 1)))
+            return fail(KNN_EINVAL, "block_size must be a power of two in [256, %d]", KNN_MAX_BLOCK);
+    }
+
+    Buffers tmp(stream);
+    DevCSR s;
+    KNN_TRY(prepare_csr(S, stream, tmp, true, true, &s));
+    if (s.max_row_nnz > 65535) return fail(KNN_EUNSUPPORTED, "an S row has more than 65535 features");
+
+    knn_index* ix = new knn_index();
+    ix->bufs = new Buffers(stream);
+    ix->stream = stream;
+    auto bail = [&](knn_status st) {
+        ix->bufs->release();
+        delete ix->bufs;
+        delete ix;
+        return st;
+    };
+    ix->n_rows = s.n_rows;
+    ix->nnz = s.nnz;
+    ix->dim = s.dim;
+    ix->dtype = s.dtype;
+    ix->max_row_nnz = s.max_row_nnz;
+    ix->max_w = s.max_w;
+    ix->max_row_sum = s.max_row_sum;
+    int32_t bs = o.block_size;
+    if (bs == 0) {
+        bs = 16384;
+        int64_t need = std::max<int64_t>(256, int64_t(1) << ilog2(std::max<int64_t>(1, s.n_rows)));
+        if (need < bs) bs = (int32_t)need;
+    }
+    ix->block_size = bs;
+    ix->block_shift = ilog2(bs);
+    ix->n_blocks = (int32_t)std::max<int64_t>(1, ceil_div(s.n_rows, bs));
+    ix->n_levels = nl;
+    // ladder: L_0 = 0; L_l = (tmax / 2) * 2^(-(nl - 1 - l) / 2) for l >= 1
+    double tmax = s.max_row_sum > 0 ? s.max_row_sum : 1.0;
+    ix->levels[0] = 0.0f;
+    for (int l = 1; l < nl; l++) ix->levels[l] = (float)(0.5 * tmax * std::pow(2.0, -0.5 * (nl - 1 - l)));
+
+    const size_t wsz = s.dtype == KNN_U8 ? 1 : 4;
+    const size_t psz = s.dtype == KNN_U8 ? 4 : 8;
+    const size_t nbins = (size_t)ix->n_blocks * (size_t)s.dim * (size_t)nl;
+    uint8_t* spw = nullptr;
+    uint8_t* post = nullptr;
+    knn_status st;
+    if ((st = ix->bufs->get(&ix->binoff, nbins + 1)) != KNN_OK) return bail(st);
+    // +16 bytes: the join reads whole aligned 16-byte vectors at list ends
+    if ((st = ix->bufs->get(&post, (size_t)s.nnz * psz + 16)) != KNN_OK) return bail(st);
+    if ((st = ix->bufs->get(&ix->s_indptr, (size_t)s.n_rows + 1)) != KNN_OK) return bail(st);
+    if ((st = ix->bufs->get(&ix->sp_d, (size_t)s.nnz)) != KNN_OK) return bail(st);
+    if ((st = ix->bufs->get(&spw, (size_t)s.nnz * wsz)) != KNN_OK) return bail(st);
+    if ((st = ix->bufs->get(&ix->n_unidx, (size_t)nl * s.n_rows)) != KNN_OK) return bail(st);
+    if ((st = ix->bufs->get(&ix->ubound, (size_t)nl * s.n_rows)) != KNN_OK) return bail(st);
+    ix->postings = post;
+    ix->sp_w = spw;
+
+    uint32_t* df = nullptr;
+    int32_t* rank = nullptr;
+    uint8_t* bucket = nullptr;
+    uint32_t* cursor = nullptr;
+    if ((st = tmp.get(&df, (size_t)s.dim)) != KNN_OK) return bail(st);
+    if ((st = tmp.get(&rank, (size_t)s.dim)) != KNN_OK) return bail(st);
+    if ((st = tmp.get(&bucket, (size_t)s.nnz)) != KNN_OK) return bail(st);
+    if ((st = tmp.get(&cursor, nbins + 1)) != KNN_OK) return bail(st);
+
+#define BAIL_CUDA(expr)                                                                        \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return bail(fail(KNN_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)));             \
+    } while (0)
+
+    BAIL_CUDA(cudaMemcpyAsync(ix->s_indptr, s.indptr, sizeof(int64_t) * (s.n_rows + 1),
+                              cudaMemcpyDeviceToDevice, stream));
+    BAIL_CUDA(cudaMemsetAsync(df, 0, sizeof(uint32_t) * s.dim, stream));
+    k_df<<<launch_blocks(s.nnz, 256, 152 * 32), 256, 0, stream>>>(s.indices, s.nnz, df);
+    BAIL_CUDA(cudaGetLastError());
+    count_launch();
+    k_rank<<<launch_blocks(s.dim, 256), 256, 0, stream>>>(df, s.dim, rank);
+    BAIL_CUDA(cudaGetLastError());
+    count_launch();
+
+    CutParams cp;
+    cp.n_rows = s.n_rows;
+    cp.n_levels = nl;
+    memcpy(cp.levels, ix->levels, sizeof(cp.levels));
+    int wblocks = launch_blocks(std::max<int64_t>(1, s.n_rows) * 32, 256, 152 * 64);
+    if (s.n_rows) {
+        if (s.dtype == KNN_U8)
+            k_cut_order<uint8_t><<<wblocks, 256, 0, stream>>>(s.indptr, s.indices, (const uint8_t*)s.values,
+                                                             rank, cp, ix->sp_d, (uint8_t*)spw, bucket,
+                                                             ix->n_unidx, ix->ubound);
+        else
+            k_cut_order<float><<<wblocks, 256, 0, stream>>>(s.indptr, s.indices, (const float*)s.values,
+                                                           rank, cp, ix->sp_d, (float*)spw, bucket,
+                                                           ix->n_unidx, ix->ubound);
+        BAIL_CUDA(cudaGetLastError());
+        count_launch();
+    }
+    BinParams bp;
+    bp.n_rows = s.n_rows;
+    bp.dim = s.dim;
+    bp.n_levels = nl;
+    bp.block_shift = ix->block_shift;
+    BAIL_CUDA(cudaMemsetAsync(ix->binoff, 0, sizeof(uint32_t) * (nbins + 1), stream));
+    if (s.n_rows) {
+        k_bin_count<<<wblocks, 256, 0, stream>>>(ix->s_indptr, ix->sp_d, bucket, bp, ix->binoff);
+        BAIL_CUDA(cudaGetLastError());
+        count_launch();
+    }
+    if ((st = exclusive_scan_u32(ix->binoff, ix->binoff, (int64_t)nbins, stream, tmp)) != KNN_OK) return bail(st);
+    BAIL_CUDA(cudaMemcpyAsync(cursor, ix->binoff, sizeof(uint32_t) * (nbins + 1), cudaMemcpyDeviceToDevice, stream));
+    if (s.n_rows) {
+        if (s.dtype == KNN_U8)
+            k_scatter<uint8_t><<<wblocks, 256, 0, stream>>>(ix->s_indptr, ix->sp_d, (const uint8_t*)spw, bucket,
+                                                           bp, cursor, post);
+        else
+            k_scatter<float><<<wblocks, 256, 0, stream>>>(ix->s_indptr, ix->sp_d, (const float*)spw, bucket,
+                                                         bp, cursor, post);
+        BAIL_CUDA(cudaGetLastError());
+        count_launch();
+    }
+    BAIL_CUDA(cudaStreamSynchronize(stream));
+#undef BAIL_CUDA
+    tmp.release();
+    *out = ix;
+    return KNN_OK;
+}
+
+extern "C" knn_status knn_index_get_info(const knn_index* ix, knn_index_info* info) {
+    if (!ix || !info) return fail(KNN_EINVAL, "NULL argument");
+    info->n_rows = ix->n_rows;
+    info->nnz = ix->nnz;
+    info->dim = ix->dim;
+    info->block_size = ix->block_size;
+    info->n_blocks = ix->n_blocks;
+    info->n_levels = ix->n_levels;
+    info->dtype = ix->dtype;
+    info->max_row_nnz = ix->max_row_nnz;
+    info->device_bytes = ix->bufs ? ix->bufs->total() : 0;
+    return KNN_OK;
+}
+
+extern "C" void knn_index_destroy(knn_index* ix) {
+    if (!ix) return;
+    if (ix->bufs) {
+        ix->bufs->release();
+        delete ix->bufs;
+    }
+    delete ix;
+}

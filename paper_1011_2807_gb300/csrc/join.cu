@@ -1,0 +1,571 @@
+// The join: Algorithm 1's loop over S blocks for each query row, with
+// Find_Matches_IIB (Algorithm 3) / Find_Matches_IIIB (Algorithm 4) per S block, and the
+// KNN candidate set with its pruneScore kept as an exact top-k.
+//
+// One CTA owns one (query row r, group of consecutive S blocks).  Per S block b:
+//   1. threshold: theta = max(floor, score of the current k-th entry); the level l is
+//      the highest with M * L_l < theta, where M = max weight of r (l = 0 in IIB mode or
+//      while theta is 0).  Section 4.4's MinPruneScore for a one-row R block is this
+//      row's own pruneScore, and M bounds maxWeight_d(B_r) for every d.
+//   2. scan: for each feature (d, r[d]), the prefix of list (b, d) indexed at level l
+//      is read with 128-bit loads and r[d] * w is added into a shared-memory
+//      accumulator of the block's S vectors (Algorithm 3/4's score map A).
+//   3. select: every accumulator entry whose upper bound (partial + M * L_l) reaches
+//      theta is checked against its exact unindexed bound, completed with the dot
+//      over its unindexed prefix (Algorithm 4's completion step, merged against r's
+//      features in shared memory), and pushed when its key beats the k-th entry.
+//   4. merge: the pushed keys and the current top-k are bitonic-sorted; the first k
+//      stay.  Keys are (score << 32) | ~id, so larger keys are better and ties go to
+//      the lower id (the strict "A[s] > pruneScore(r)" of Algorithms 2-4 with S
+//      visited in ascending id).
+// With several groups per row, the groups publish their k-th key through a per-row
+// atomicMax floor (a lower bound on the final k-th key) and a second kernel merges
+// the groups' lists.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace knn {
+
+typedef unsigned long long u64;
+
+constexpr int KMAX = KNN_MAX_K;
+constexpr int SORT_CAP = 1024;            // keys in the merge buffer (pushed + current top-k)
+constexpr int PUSH_CAP = SORT_CAP - KMAX;  // pushed candidates between merges
+
+__device__ __forceinline__ u64 make_key(uint32_t score_bits, uint32_t gid) {
+    return ((u64)score_bits << 32) | (u64)(0xFFFFFFFFu - gid);
+}
+__device__ __forceinline__ uint32_t key_gid(u64 key) { return 0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull); }
+
+template <class W>
+struct JT;
+template <>
+struct JT<uint8_t> {
+    using Acc = int32_t;
+    using Post = uint32_t;
+    static constexpr int PER_VEC = 4;  // postings per 16-byte load
+    __device__ static uint32_t score_bits(int32_t v) { return (uint32_t)v; }
+    __device__ static double score_of_bits(uint32_t b) { return (double)b; }
+    __device__ static int32_t post_lid(uint32_t p) { return (int32_t)(p & 0xFFFFu); }
+    __device__ static int32_t post_w(uint32_t p) { return (int32_t)(p >> 16); }
+    __device__ static double ubound(uint32_t b) { return (double)b; }
+    __device__ static u64 floor_key(float tau) {
+        if (!(tau > 1.0f)) return (u64)1 << 32;
+        double c = ceil((double)tau);
+        if (c >= 4294967295.0) return (u64)0xFFFFFFFFull << 32;
+        return (u64)(uint32_t)c << 32;
+    }
+    static constexpr double SLACK = 0.0;
+};
+template <>
+struct JT<float> {
+    using Acc = float;
+    using Post = uint2;
+    static constexpr int PER_VEC = 2;
+    __device__ static uint32_t score_bits(float v) { return __float_as_uint(v); }
+    __device__ static double score_of_bits(uint32_t b) { return (double)__uint_as_float(b); }
+    __device__ static int32_t post_lid(uint2 p) { return (int32_t)p.x; }
+    __device__ static float post_w(uint2 p) { return __uint_as_float(p.y); }
+    __device__ static double ubound(uint32_t b) { return (double)__uint_as_float(b); }
+    __device__ static u64 floor_key(float tau) {
+        if (!(tau > 0.0f)) return (u64)1 << 32;
+        return (u64)__float_as_uint(tau) << 32;
+    }
+    // fp32 sums may differ from the real sum by a few ulps; widen bounds a little
+    static constexpr double SLACK = 1.0 / (1 << 20);
+};
+
+struct JoinParams {
+    int64_t n_rows;
+    const int64_t* r_indptr;
+    const int32_t* r_idx;
+    const void* r_val;
+    int64_t n_s;
+    int32_t dim, n_blocks, n_levels, block_shift;
+    const uint32_t* binoff;
+    const void* postings;
+    const int64_t* s_indptr;
+    const int32_t* sp_d;
+    const void* sp_w;
+    const uint16_t* n_unidx;
+    const uint32_t* ubound;
+    float levels[KNN_MAX_LEVELS];
+    int32_t k, groups, blocks_per_group, iiib, max_r_nnz;
+    const float* init_thr;
+    u64* part_keys;
+    int32_t* out_ids;
+    void* out_scores;
+    int32_t* n_found;
+    u64* floor_keys;
+    unsigned long long* touched;
+};
+
+struct SmemLayout {
+    size_t acc, rf_d, rf_w, lbeg, lend, topk, sort, total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline SmemLayout smem_layout(int nb, int max_r_nnz) {
+    SmemLayout L;
+    size_t o = 0;
+    L.acc = o;  o = align16(o + (size_t)nb * 4);
+    L.rf_d = o; o = align16(o + (size_t)max_r_nnz * 4);
+    L.rf_w = o; o = align16(o + (size_t)max_r_nnz * 4);
+    L.lbeg = o; o = align16(o + (size_t)max_r_nnz * 4);
+    L.lend = o; o = align16(o + (size_t)max_r_nnz * 4);
+    L.topk = o; o = align16(o + (size_t)KMAX * 8);
+    L.sort = o; o = align16(o + (size_t)SORT_CAP * 8);
+    L.total = o;
+    return L;
+}
+
+// Descending bitonic sort of buf[0..P), P a power of two, all threads of the CTA.
+__device__ void cta_bitonic_desc(u64* buf, int P) {
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < (P >> 1); i += blockDim.x) {
+                int lo = 2 * i - (i & (stride - 1));
+                int hi = lo + stride;
+                bool desc = (lo & size) == 0;
+                u64 a = buf[lo], b = buf[hi];
+                if ((a < b) == desc) {
+                    buf[lo] = b;
+                    buf[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+struct CtaState {
+    int cnt;        // pushed candidates in the sort buffer
+    int size;       // entries in topk
+    int level;
+    int pending;    // candidates still masked (overflow rounds)
+    double theta;   // pruning threshold of the current block
+    u64 floor;      // keys below this never qualify
+    u64 kth;        // current k-th key (0 while fewer than k)
+    double M;       // largest weight of r
+};
+
+// merge pushed keys with topk; all threads
+__device__ void merge_topk(u64* topk, u64* sortbuf, CtaState& st, int k) {
+    __syncthreads();
+    int cnt = st.cnt;
+    if (cnt == 0) return;
+    int m = st.size;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) sortbuf[cnt + i] = topk[i];
+    int n = cnt + m;
+    int P = 2;
+    while (P < n) P <<= 1;
+    for (int i = n + threadIdx.x; i < P; i += blockDim.x) sortbuf[i] = 0ull;
+    __syncthreads();
+    cta_bitonic_desc(sortbuf, P);
+    int keep = min(k, n);
+    for (int i = threadIdx.x; i < keep; i += blockDim.x) topk[i] = sortbuf[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st.size = keep;
+        st.cnt = 0;
+        st.kth = keep == k ? topk[k - 1] : 0ull;
+    }
+    __syncthreads();
+}
+
+template <class W>
+__device__ __forceinline__ typename JT<W>::Acc lookup_r(const int32_t* rf_d, const typename JT<W>::Acc* rf_w,
+                                                        int n, int32_t d) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (rf_d[mid] < d) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < n && rf_d[lo] == d) ? rf_w[lo] : (typename JT<W>::Acc)0;
+}
+
+template <class W>
+__global__ void __launch_bounds__(1024) k_join(JoinParams p) {
+    using Acc = typename JT<W>::Acc;
+    using Post = typename JT<W>::Post;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ CtaState st;
+    __shared__ double red_d[32];
+    __shared__ unsigned long long red_u[32];
+
+    const int nb = 1 << p.block_shift;
+    const SmemLayout L = smem_layout(nb, p.max_r_nnz);
+    Acc* acc = (Acc*)(smem + L.acc);
+    int32_t* rf_d = (int32_t*)(smem + L.rf_d);
+    Acc* rf_w = (Acc*)(smem + L.rf_w);
+    uint32_t* lbeg = (uint32_t*)(smem + L.lbeg);
+    uint32_t* lend = (uint32_t*)(smem + L.lend);
+    u64* topk = (u64*)(smem + L.topk);
+    u64* sortbuf = (u64*)(smem + L.sort);
+
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
+    const int64_t row = blockIdx.x / p.groups;
+    const int g = blockIdx.x - (int)(row * p.groups);
+    const int64_t ra = p.r_indptr[row];
+    const int rn = (int)(p.r_indptr[row + 1] - ra);
+    const int b0 = g * p.blocks_per_group;
+    const int b1 = min(p.n_blocks, b0 + p.blocks_per_group);
+
+    // load r (ascending d) and its largest weight
+    double mloc = 0.0;
+    for (int i = tid; i < rn; i += T) {
+        rf_d[i] = p.r_idx[ra + i];
+        Acc w = (Acc)((const W*)p.r_val)[ra + i];
+        rf_w[i] = w;
+        mloc = fmax(mloc, (double)w);
+    }
+    for (int o = 16; o > 0; o >>= 1) mloc = fmax(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
+    if (lane == 0) red_d[warp] = mloc;
+    // clear the accumulator
+    for (int i = tid * 4; i < nb; i += T * 4) *(int4*)(acc + i) = make_int4(0, 0, 0, 0);
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int w = 0; w < nwarps; w++) m = fmax(m, red_d[w]);
+        st.M = m;
+        st.size = 0;
+        st.cnt = 0;
+        st.kth = 0ull;
+        st.floor = p.init_thr ? JT<W>::floor_key(p.init_thr[row]) : ((u64)1 << 32);
+    }
+    __syncthreads();
+
+    unsigned long long touched = 0;
+    const int chunks = nb / (T * 4);  // <= 16 by construction (mask has 64 bits)
+
+    for (int b = (rn > 0 ? b0 : b1); b < b1; b++) {
+        // ---- 1. threshold and level ----
+        if (tid == 0) {
+            u64 fl = st.floor;
+            if (p.floor_keys) {
+                u64 shared = *(volatile u64*)(p.floor_keys + row);
+                if (shared > fl) fl = shared;
+            }
+            st.floor = fl;
+            u64 eff = st.kth > fl ? st.kth : fl;
+            double theta = JT<W>::score_of_bits((uint32_t)(eff >> 32));
+            st.theta = theta;
+            int level = 0;
+            if (p.iiib) {
+                for (int l = p.n_levels - 1; l >= 1; l--) {
+                    double lim = st.M * (double)p.levels[l] * (1.0 + JT<W>::SLACK);
+                    if (lim < theta) {
+                        level = l;
+                        break;
+                    }
+                }
+            }
+            st.level = level;
+        }
+        __syncthreads();
+        const int level = st.level;
+        // ---- list ranges of r's features in block b at this level ----
+        const size_t bbase = (size_t)b * (size_t)p.dim;
+        for (int i = tid; i < rn; i += T) {
+            size_t base = (bbase + (size_t)rf_d[i]) * (size_t)p.n_levels;
+            lbeg[i] = p.binoff[base];
+            lend[i] = p.binoff[base + (size_t)(p.n_levels - level)];
+        }
+        __syncthreads();
+        // ---- 2. scan: acc[lid] += r[d] * w over the indexed prefixes ----
+        {
+            const Post* post = (const Post*)p.postings;
+            constexpr int V = JT<W>::PER_VEC;
+            for (int i = warp; i < rn; i += nwarps) {
+                const uint32_t beg = lbeg[i], end = lend[i];
+                if (beg >= end) continue;
+                const Acc rw = rf_w[i];
+                touched += (lane == 0) ? (end - beg) : 0;
+                uint32_t q = (beg & ~(uint32_t)(V - 1)) + (uint32_t)lane * V;
+                for (; q < end; q += 32 * V * 2) {
+                    uint4 v0 = *(const uint4*)(post + q);
+                    uint32_t q1 = q + 32 * V;
+                    uint4 v1 = make_uint4(0, 0, 0, 0);
+                    if (q1 < end) v1 = *(const uint4*)(post + q1);
+                    const Post* e0 = (const Post*)&v0;
+                    const Post* e1 = (const Post*)&v1;
+#pragma unroll
+                    for (int e = 0; e < V; e++) {
+                        uint32_t pe = q + e;
+                        if (pe >= beg && pe < end)
+                            atomicAdd(&acc[JT<W>::post_lid(e0[e])], rw * JT<W>::post_w(e0[e]));
+                    }
+#pragma unroll
+                    for (int e = 0; e < V; e++) {
+                        uint32_t pe = q1 + e;
+                        if (pe < end) atomicAdd(&acc[JT<W>::post_lid(e1[e])], rw * JT<W>::post_w(e1[e]));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // ---- 3. select ----
+        const double theta = st.theta;
+        const double M = st.M;
+        const double lvl_bound = level > 0 ? M * (double)p.levels[level] : 0.0;
+        const int64_t gbase = (int64_t)b << p.block_shift;
+        unsigned long long mask = 0ull;
+        int mycount = 0;
+        for (int c = 0; c < chunks; c++) {
+            int lid0 = c * T * 4 + tid * 4;
+            int4 raw = *(int4*)(acc + lid0);
+            Acc* v = (Acc*)&raw;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                bool keep = false;
+                if (v[e] > (Acc)0) {
+                    double ub = ((double)v[e] + lvl_bound) * (1.0 + JT<W>::SLACK);
+                    keep = ub >= theta;
+                }
+                if (keep) {
+                    mask |= 1ull << (c * 4 + e);
+                    mycount++;
+                } else {
+                    v[e] = (Acc)0;
+                }
+            }
+            *(int4*)(acc + lid0) = raw;
+        }
+        // total cheap candidates
+        int wsum = mycount;
+        for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+        if (lane == 0) red_u[warp] = (unsigned long long)wsum;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long t = 0;
+            for (int w = 0; w < nwarps; w++) t += red_u[w];
+            st.pending = (int)t;
+        }
+        __syncthreads();
+        const bool one_round = st.pending <= PUSH_CAP;
+        const int per_round = one_round ? 64 : max(1, PUSH_CAP / T);
+        while (true) {
+            int done_here = 0;
+            const u64 kth = st.kth;
+            const u64 fl = st.floor;
+            const double th = one_round ? theta
+                                        : fmax(theta, JT<W>::score_of_bits((uint32_t)((kth > fl ? kth : fl) >> 32)));
+            while (mask && done_here < per_round) {
+                int bit = __ffsll(mask) - 1;
+                mask &= mask - 1;
+                done_here++;
+                int c = bit >> 2, e = bit & 3;
+                int lid = c * T * 4 + tid * 4 + e;
+                Acc v = acc[lid];
+                acc[lid] = (Acc)0;
+                int64_t gid = gbase + lid;
+                // cheap bound against the (possibly raised) threshold
+                if (((double)v + lvl_bound) * (1.0 + JT<W>::SLACK) < th) continue;
+                Acc full = v;
+                if (level > 0) {
+                    double ub = ((double)v + M * JT<W>::ubound(p.ubound[(int64_t)level * p.n_s + gid])) *
+                                (1.0 + JT<W>::SLACK);
+                    if (ub < th) continue;
+                    const int64_t j0 = p.s_indptr[gid];
+                    const int m = p.n_unidx[(int64_t)level * p.n_s + gid];
+                    Acc res = (Acc)0;
+                    for (int q = 0; q < m; q++) {
+                        int32_t d = p.sp_d[j0 + q];
+                        Acc w = (Acc)((const W*)p.sp_w)[j0 + q];
+                        res += lookup_r<W>(rf_d, rf_w, rn, d) * w;
+                    }
+                    full = v + res;
+                }
+                u64 key = make_key(JT<W>::score_bits(full), (uint32_t)gid);
+                if (key >= fl && key > kth) {
+                    int slot = atomicAdd(&st.cnt, 1);
+                    sortbuf[slot] = key;
+                }
+            }
+            if (one_round) {
+                merge_topk(topk, sortbuf, st, p.k);
+                break;
+            }
+            merge_topk(topk, sortbuf, st, p.k);
+            if (!__syncthreads_or(mask != 0ull)) break;
+        }
+        // publish this group's k-th key as a floor for the other groups of the row
+        if (tid == 0 && p.floor_keys && st.size == p.k) atomicMax(p.floor_keys + row, st.kth);
+        __syncthreads();
+    }
+
+    // ---- output ----
+    if (p.groups == 1) {
+        for (int q = tid; q < p.k; q += T) {
+            u64 key = q < st.size ? topk[q] : 0ull;
+            int64_t o = row * p.k + q;
+            p.out_ids[o] = key ? (int32_t)key_gid(key) : -1;
+            ((uint32_t*)p.out_scores)[o] = key ? (uint32_t)(key >> 32) : 0u;
+        }
+        if (tid == 0 && p.n_found) p.n_found[row] = st.size;
+    } else {
+        for (int q = tid; q < p.k; q += T)
+            p.part_keys[((int64_t)row * p.groups + g) * p.k + q] = q < st.size ? topk[q] : 0ull;
+    }
+    // posting counter
+    if (p.touched) {
+        for (int o = 16; o > 0; o >>= 1) touched += __shfl_xor_sync(0xffffffffu, touched, o);
+        if (lane == 0 && touched) atomicAdd(p.touched, touched);
+    }
+}
+
+// one CTA per row: top-k of the groups' lists
+__global__ void k_merge_groups(const u64* __restrict__ part, int64_t n_rows, int groups, int k, int P,
+                               int32_t* out_ids, uint32_t* out_scores, int32_t* n_found) {
+    extern __shared__ u64 buf[];
+    int64_t row = blockIdx.x;
+    int n = groups * k;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) buf[i] = i < n ? part[row * n + i] : 0ull;
+    __syncthreads();
+    cta_bitonic_desc(buf, P);
+    for (int q = threadIdx.x; q < k; q += blockDim.x) {
+        u64 key = buf[q];
+        out_ids[row * k + q] = key ? (int32_t)key_gid(key) : -1;
+        out_scores[row * k + q] = key ? (uint32_t)(key >> 32) : 0u;
+    }
+    if (n_found && threadIdx.x == 0) {
+        int c = 0;
+        for (int q = 0; q < k; q++) c += buf[q] != 0ull;
+        n_found[row] = c;
+    }
+}
+
+}  // namespace knn
+
+using namespace knn;
+
+extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k, const knn_join_opts* opts,
+                               int32_t* out_ids, void* out_scores, void* stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!ix) return fail(KNN_EINVAL, "index is NULL");
+    if (!R) return fail(KNN_EINVAL, "R is NULL");
+    if (k < 1) return fail(KNN_EINVAL, "k must be >= 1");
+    if (k > KNN_MAX_K) return fail(KNN_EUNSUPPORTED, "k > %d", KNN_MAX_K);
+    if (R->dim != ix->dim) return fail(KNN_EINVAL, "R has dim %d, the index %d", R->dim, ix->dim);
+    if (R->dtype != ix->dtype) return fail(KNN_EINVAL, "R and the index have different dtypes");
+    knn_join_opts o = {};
+    if (opts) o = *opts;
+    if (o.mode != KNN_MODE_IIIB && o.mode != KNN_MODE_IIB) return fail(KNN_EINVAL, "unknown mode");
+    if (R->n_rows > 0 && (!out_ids || !out_scores)) return fail(KNN_EINVAL, "outputs are NULL");
+
+    Buffers tmp(stream);
+    DevCSR r;
+    KNN_TRY(prepare_csr(R, stream, tmp, !o.skip_validation, true, &r));
+    if (r.n_rows == 0) return KNN_OK;
+    if (ix->dtype == KNN_U8) {
+        double bound = std::min(r.max_row_sum * ix->max_w, ix->max_row_sum * r.max_w);
+        if (bound >= 2147483647.0) return fail(KNN_EUNSUPPORTED, "uint8 scores could overflow int32");
+    }
+    const int nb = ix->block_size;
+    int T = o.threads ? o.threads : 256;
+    if (T < 128 || T > 1024 || (T & 31)) return fail(KNN_EINVAL, "threads must be a multiple of 32 in [128, 1024]");
+    // each thread owns 4 accumulator entries per chunk and a 64-bit candidate mask:
+    // T * 4 <= nb and nb / (T * 4) <= 16 (nb and T are powers of two times 32)
+    while (nb / (T * 4) > 16) T *= 2;
+    while (T > 32 && nb < T * 4) T /= 2;
+    if (nb % (T * 4) || nb / (T * 4) > 16 || T > 1024)
+        return fail(KNN_EUNSUPPORTED, "block size %d does not fit %d threads", nb, T);
+    const int max_r = std::max(1, r.max_row_nnz);
+    SmemLayout L = smem_layout(nb, max_r);
+    int dev = 0;
+    KNN_CUDA_TRY(cudaGetDevice(&dev));
+    int smem_optin = 0, n_sm = 0;
+    KNN_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    KNN_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    const size_t static_smem = sizeof(CtaState) + 32 * 8 * 2 + 64;
+    if (L.total + static_smem > (size_t)smem_optin)
+        return fail(KNN_EUNSUPPORTED, "a row with %d features and S blocks of %d need %zu bytes of shared memory (> %d)",
+                    max_r, nb, L.total, smem_optin);
+
+    // groups of S blocks per row
+    int per_sm = std::max(1, std::min((int)(228 * 1024 / (L.total + static_smem + 1024)), 2048 / T));
+    int groups = o.s_groups;
+    if (groups <= 0) {
+        int64_t target = (int64_t)n_sm * per_sm * 4;
+        groups = (int)std::min<int64_t>(ix->n_blocks, std::max<int64_t>(1, ceil_div(target, r.n_rows)));
+    }
+    groups = std::max(1, std::min(groups, ix->n_blocks));
+    groups = std::min(groups, std::max(1, 4096 / k));
+    int bpg = (int)ceil_div(ix->n_blocks, groups);
+    groups = (int)ceil_div(ix->n_blocks, bpg);
+    if ((int64_t)r.n_rows * groups > (int64_t)INT32_MAX) return fail(KNN_EUNSUPPORTED, "too many rows");
+
+    int32_t* d_ids = out_ids;
+    uint32_t* d_sc = (uint32_t*)out_scores;
+    if (o.outputs_on_host) {
+        KNN_TRY(tmp.get(&d_ids, (size_t)r.n_rows * k));
+        KNN_TRY(tmp.get(&d_sc, (size_t)r.n_rows * k));
+    }
+    JoinParams p;
+    memset(&p, 0, sizeof(p));
+    p.n_rows = r.n_rows;
+    p.r_indptr = r.indptr;
+    p.r_idx = r.indices;
+    p.r_val = r.values;
+    p.n_s = ix->n_rows;
+    p.dim = ix->dim;
+    p.n_blocks = ix->n_blocks;
+    p.n_levels = ix->n_levels;
+    p.block_shift = ix->block_shift;
+    p.binoff = ix->binoff;
+    p.postings = ix->postings;
+    p.s_indptr = ix->s_indptr;
+    p.sp_d = ix->sp_d;
+    p.sp_w = ix->sp_w;
+    p.n_unidx = ix->n_unidx;
+    p.ubound = ix->ubound;
+    memcpy(p.levels, ix->levels, sizeof(p.levels));
+    p.k = k;
+    p.groups = groups;
+    p.blocks_per_group = bpg;
+    p.iiib = o.mode == KNN_MODE_IIIB && ix->n_levels > 1;
+    p.max_r_nnz = max_r;
+    p.init_thr = o.init_threshold;
+    p.out_ids = d_ids;
+    p.out_scores = d_sc;
+    p.n_found = o.n_found;
+    p.touched = (unsigned long long*)o.postings_scanned;
+    if (groups > 1) {
+        KNN_TRY(tmp.get(&p.part_keys, (size_t)r.n_rows * groups * k));
+        KNN_TRY(tmp.get(&p.floor_keys, (size_t)r.n_rows));
+        KNN_CUDA_TRY(cudaMemsetAsync(p.floor_keys, 0, sizeof(u64) * r.n_rows, stream));
+    }
+    int64_t grid = r.n_rows * groups;
+    if (ix->dtype == KNN_U8) {
+        KNN_CUDA_TRY(cudaFuncSetAttribute(k_join<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+        k_join<uint8_t><<<(unsigned)grid, T, L.total, stream>>>(p);
+    } else {
+        KNN_CUDA_TRY(cudaFuncSetAttribute(k_join<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+        k_join<float><<<(unsigned)grid, T, L.total, stream>>>(p);
+    }
+    KNN_CUDA_TRY(cudaGetLastError());
+    count_launch();
+    if (groups > 1) {
+        int P = 2;
+        while (P < groups * k) P <<= 1;
+        KNN_CUDA_TRY(cudaFuncSetAttribute(k_merge_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, P * 8));
+        k_merge_groups<<<(unsigned)r.n_rows, 256, P * 8, stream>>>(p.part_keys, r.n_rows, groups, k, P, d_ids, d_sc,
+                                                                    o.n_found);
+        KNN_CUDA_TRY(cudaGetLastError());
+        count_launch();
+    }
+    if (o.outputs_on_host) {
+        KNN_CUDA_TRY(cudaMemcpyAsync(out_ids, d_ids, sizeof(int32_t) * r.n_rows * k, cudaMemcpyDeviceToHost, stream));
+        KNN_CUDA_TRY(cudaMemcpyAsync(out_scores, d_sc, sizeof(uint32_t) * r.n_rows * k, cudaMemcpyDeviceToHost, stream));
+        KNN_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
+    return KNN_OK;
+}

@@ -1,0 +1,311 @@
+"""Parity of the CUDA join (through the C ABI) with the CPU oracle."""
+import numpy as np
+import pytest
+
+from paper_1011_2807_gb300 import synth
+import compare
+import goldens
+import refdefs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def knn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1011_2807_gb300 as knn
+    knn.lib()
+    return knn
+
+
+def run(knn, S, R, k, device_r=True, **kw):
+    import torch
+    bopts = {x: kw.pop(x) for x in ("block_size", "n_levels") if x in kw}
+    idx = knn.knn_join_build_index(S, **bopts)
+    Rin = knn.DeviceCSR.from_host(R) if device_r else R
+    ids, sc = knn.knn_join(idx, Rin, k, **kw)
+    torch.cuda.synchronize()
+    out = (ids.cpu().numpy(), sc.cpu().numpy())
+    idx.close()
+    return out
+
+
+def random_u8(n, dim, nnz_hi, seed, wmax=100, nnz_lo=0):
+    rng = np.random.default_rng(seed)
+    rows = []
+    for _ in range(n):
+        m = int(rng.integers(nnz_lo, min(nnz_hi, dim) + 1))
+        d = rng.choice(dim, size=m, replace=False)
+        w = rng.integers(1, wmax + 1, size=m)
+        rows.append(list(zip(d.tolist(), w.tolist())))
+    return synth.from_rows(rows, dim, np.uint8)
+
+
+# ----------------------------------------------------------------------------------
+# hand-worked examples
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["iib", "iiib"])
+def test_h1(knn, oracle_mod, mode):
+    g = goldens.load("h1_topk.txt")
+    for k, exp in g["cases"]:
+        ids, sc = run(knn, g["S"], g["R"], k, mode=mode)
+        eids, esc = goldens.expected_arrays(exp, g["R"].n_rows, k)
+        np.testing.assert_array_equal(ids, eids)
+        np.testing.assert_array_equal(sc, esc)
+
+
+def test_h2(knn, oracle_mod):
+    g = goldens.load("h2_iiib_trace.txt")
+    (k, exp), = g["cases"]
+    ids, sc = run(knn, g["S"], g["R"], k, block_size=256)
+    eids, esc = goldens.expected_arrays(exp, g["R"].n_rows, k)
+    np.testing.assert_array_equal(ids, eids)
+    np.testing.assert_array_equal(sc, esc)
+
+
+# ----------------------------------------------------------------------------------
+# uint8: bit-exact against the oracle
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["iib", "iiib"])
+@pytest.mark.parametrize("bs,nl", [(256, 1), (256, 16), (1024, 4), (2048, 32)])
+@pytest.mark.parametrize("k", [1, 5, 64])
+def test_spectrum_u8_exact(knn, oracle_mod, mode, bs, nl, k):
+    S = synth.spectrum_u8(5000, 31, role="S")          # 20 blocks of 256: a ragged tail
+    R = synth.spectrum_u8(120, 32, role="R")
+    eids, esc, _ = oracle_mod.iib_join(R, S, k, threads=8)
+    ids, sc = run(knn, S, R, k, mode=mode, block_size=bs, n_levels=nl)
+    compare.assert_exact(ids, sc, eids, esc, f"mode={mode} bs={bs} nl={nl} k={k}")
+
+
+@pytest.mark.parametrize("groups", [1, 2, 7, 0])
+def test_s_groups(knn, oracle_mod, groups):
+    S = synth.spectrum_u8(9000, 41, role="S")
+    R = synth.spectrum_u8(60, 42, role="R")
+    eids, esc, _ = oracle_mod.iib_join(R, S, 10, threads=8)
+    ids, sc = run(knn, S, R, 10, block_size=512, s_groups=groups)
+    compare.assert_exact(ids, sc, eids, esc, f"groups={groups}")
+
+
+@pytest.mark.parametrize("threads", [128, 256, 512, 1024])
+def test_threads(knn, oracle_mod, threads):
+    S = synth.spectrum_u8(6000, 51, role="S")
+    R = synth.spectrum_u8(50, 52, role="R")
+    eids, esc, _ = oracle_mod.iib_join(R, S, 5, threads=8)
+    ids, sc = run(knn, S, R, 5, block_size=4096, threads=threads)
+    compare.assert_exact(ids, sc, eids, esc, f"threads={threads}")
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_small_dims_many_ties(knn, oracle_mod, seed):
+    # few dimensions and weights in {1,2}: scores tie everywhere
+    S = random_u8(700, 12, 6, 60 + seed, wmax=2)
+    R = random_u8(40, 12, 6, 70 + seed, wmax=2)
+    for k in (1, 3, 20, 64):
+        eids, esc, _ = oracle_mod.bf_join(R, S, k, threads=8)
+        ids, sc = run(knn, S, R, k, block_size=256)
+        compare.assert_exact(ids, sc, eids, esc, f"ties k={k}")
+
+
+def test_max_weights_and_long_rows(knn, oracle_mod):
+    # weight 255 everywhere, R rows of up to 2,000 features, S rows of up to 300
+    rng = np.random.default_rng(5)
+    S = random_u8(1500, 4000, 300, 81, wmax=255, nnz_lo=200)
+    R = random_u8(20, 4000, 2000, 82, wmax=255, nnz_lo=1500)
+    S.values[:] = 255
+    eids, esc, _ = oracle_mod.iib_join(R, S, 8, threads=8)
+    ids, sc = run(knn, S, R, 8, block_size=512)
+    compare.assert_exact(ids, sc, eids, esc, "max weights")
+
+
+def test_config2_scaled(knn, oracle_mod):
+    R, S, k = synth.config2(n_r=400, n_s=100000)
+    eids, esc, _ = oracle_mod.iib_join(R, S, k, threads=8)
+    for mode in ("iib", "iiib"):
+        ids, sc = run(knn, S, R, k, mode=mode)
+        compare.assert_exact(ids, sc, eids, esc, f"config2 scaled {mode}")
+
+
+# ----------------------------------------------------------------------------------
+# float32: 1e-5 relative, boundary ties allowed
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["iib", "iiib"])
+def test_config1_scaled_f32(knn, oracle_mod, mode):
+    R, S, k = synth.config1(scale=0.2)
+    eids, esc, _ = oracle_mod.iib_join(R, S, k, threads=8)
+    ids, sc = run(knn, S, R, k, mode=mode, block_size=512)
+    compare.assert_close(R, S, list(range(R.n_rows)), ids, sc, eids, esc, what=f"config1 {mode}")
+
+
+def test_config1_full_f32(knn, oracle_mod):
+    R, S, k = synth.config1()
+    eids, esc, _ = oracle_mod.iib_join(R, S, k, threads=8)
+    ids, sc = run(knn, S, R, k)
+    compare.assert_close(R, S, list(range(R.n_rows)), ids, sc, eids, esc, what="config1 full")
+
+
+def test_zipf_normalised_f32(knn, oracle_mod):
+    S = synth.zipf_f32(3000, 91, dim=2000, nnz_hi=200)
+    R = synth.zipf_f32(40, 92, dim=2000, nnz_hi=200)
+    eids, esc, _ = oracle_mod.iib_join(R, S, 20, threads=8)
+    for mode in ("iib", "iiib"):
+        ids, sc = run(knn, S, R, 20, mode=mode, block_size=512)
+        compare.assert_close(R, S, list(range(R.n_rows)), ids, sc, eids, esc, what=f"zipf {mode}")
+
+
+# ----------------------------------------------------------------------------------
+# degenerate inputs
+# ----------------------------------------------------------------------------------
+
+def test_degenerate(knn, oracle_mod):
+    import torch
+    S = synth.from_rows([[(1, 2), (3, 1)], [], [(3, 2)], [(2, 4)], [(1, 1), (3, 1)]], 6)
+    # R with an empty row and a row without overlap
+    R = synth.from_rows([[], [(0, 9)], [(1, 1), (3, 1)]], 6)
+    ids, sc = run(knn, S, R, 7)
+    eids, esc, _ = oracle_mod.bf_join(R, S, 7)
+    compare.assert_exact(ids, sc, eids, esc, "degenerate")
+    # empty R
+    idx = knn.knn_join_build_index(S)
+    e = synth.from_rows([], 6)
+    ids, sc = knn.knn_join(idx, e, 3)
+    assert ids.shape == (0, 3)
+    # all S rows identical: every score ties, ids ascending
+    same = synth.from_rows([[(2, 3), (5, 1)]] * 1000, 8)
+    ids, sc = run(knn, same, same.slice_rows(0, 2), 6, block_size=256, s_groups=3)
+    assert ids.tolist() == [[0, 1, 2, 3, 4, 5]] * 2 and sc.tolist() == [[10] * 6] * 2
+    # empty S
+    empty_s = synth.from_rows([[]] * 3, 6)
+    ids, sc = run(knn, empty_s, R, 2)
+    assert (ids == -1).all() and (sc == 0).all()
+    idx.close()
+
+
+def test_host_inputs_and_host_outputs(knn, oracle_mod):
+    S = synth.spectrum_u8(4000, 61, role="S")
+    R = synth.spectrum_u8(30, 62, role="R")
+    eids, esc, _ = oracle_mod.iib_join(R, S, 5, threads=8)
+    idx = knn.knn_join_build_index(S)
+    ids, sc = knn.knn_join(idx, R, 5, outputs_on_host=True)
+    compare.assert_exact(ids.numpy(), sc.numpy(), eids, esc, "host in/out")
+    idx.close()
+
+
+# ----------------------------------------------------------------------------------
+# input validation (host-side error codes, no fault)
+# ----------------------------------------------------------------------------------
+
+def test_validation_errors(knn):
+    from paper_1011_2807_gb300.binding import KNN_EINVAL, KNN_EUNSUPPORTED, KnnError
+    good = synth.from_rows([[(1, 2), (3, 1)], [(0, 1)]], 6)
+    idx = knn.knn_join_build_index(good)
+    bad_cases = []
+    b = synth.from_rows([[(1, 2), (3, 1)]], 6); b.indices[:] = [3, 1]; bad_cases.append(("unsorted", b))
+    b = synth.from_rows([[(1, 2), (3, 1)]], 6); b.indices[:] = [1, 1]; bad_cases.append(("duplicate", b))
+    b = synth.from_rows([[(1, 2), (3, 1)]], 6); b.indices[1] = 6; bad_cases.append(("d >= dim", b))
+    b = synth.from_rows([[(1, 2), (3, 1)]], 6); b.indices[0] = -1; bad_cases.append(("d < 0", b))
+    b = synth.from_rows([[(1, 2), (3, 1)]], 6); b.values[0] = 0; bad_cases.append(("w = 0", b))
+    b = synth.from_rows([[(1, 2), (3, 1)], [(2, 1)]], 6); b.indptr[1] = 5; bad_cases.append(("indptr", b))
+    f = synth.from_rows([[(1, 0.5), (3, 1.0)]], 6, np.float32); f.values[0] = np.nan
+    for name, bcsr in bad_cases:
+        for dev in (False, True):
+            with pytest.raises(KnnError) as e:
+                knn.knn_join(idx, knn.DeviceCSR.from_host(bcsr) if dev else bcsr, 2)
+            assert e.value.status == KNN_EINVAL, name
+            with pytest.raises(KnnError):
+                knn.knn_join_build_index(bcsr)
+    with pytest.raises(KnnError) as e:
+        knn.knn_join_build_index(f)
+    assert e.value.status == KNN_EINVAL
+    with pytest.raises(KnnError) as e:
+        knn.knn_join(idx, good, 65)
+    assert e.value.status == KNN_EUNSUPPORTED
+    with pytest.raises(KnnError) as e:
+        knn.knn_join(idx, good, 0)
+    assert e.value.status == KNN_EINVAL
+    with pytest.raises(KnnError) as e:      # dim mismatch
+        knn.knn_join(idx, synth.from_rows([[(1, 2)]], 7), 2)
+    assert e.value.status == KNN_EINVAL
+    with pytest.raises(KnnError) as e:      # dtype mismatch
+        knn.knn_join(idx, synth.from_rows([[(1, 0.5)]], 6, np.float32), 2)
+    assert e.value.status == KNN_EINVAL
+    idx.close()
+
+
+# ----------------------------------------------------------------------------------
+# a learned start threshold: rows keep only scores >= tau, n_found counts them
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["iib", "iiib"])
+def test_init_threshold(knn, oracle_mod, mode):
+    import torch
+    S = synth.spectrum_u8(8000, 71, role="S")
+    R = synth.spectrum_u8(80, 72, role="R")
+    k = 10
+    eids, esc, _ = oracle_mod.iib_join(R, S, 64, threads=8)
+    rng = np.random.default_rng(3)
+    # thresholds around each row's k-th score: some rows over-predicted, some under
+    tau = (esc[:, k - 1] * rng.uniform(0.5, 1.5, size=R.n_rows)).astype(np.float32)
+    tau[0] = 0.0
+    tau[1] = np.float32(esc[1, k - 1])          # exactly the k-th score (inclusive)
+    tau[2] = np.float32(1e9)                    # nothing passes
+    t_tau = torch.from_numpy(tau).cuda()
+    found = torch.zeros(R.n_rows, dtype=torch.int32, device="cuda")
+    idx = knn.knn_join_build_index(S, block_size=1024)
+    ids, sc = knn.knn_join(idx, knn.DeviceCSR.from_host(R), k, mode=mode, init_threshold=t_tau, n_found=found)
+    torch.cuda.synchronize()
+    ids, sc, found = ids.cpu().numpy(), sc.cpu().numpy(), found.cpu().numpy()
+    for i in range(R.n_rows):
+        keep = esc[i] >= max(tau[i], 1e-30)
+        want = min(k, int(keep.sum()))
+        assert found[i] == want, (i, found[i], want)
+        np.testing.assert_array_equal(ids[i, :want], eids[i, :want])
+        np.testing.assert_array_equal(sc[i, :want], esc[i, :want])
+        assert (ids[i, want:] == -1).all()
+    idx.close()
+
+
+# ----------------------------------------------------------------------------------
+# posting counters: IIB scans exactly the eq. 4 count; IIIB scans no more
+# ----------------------------------------------------------------------------------
+
+def test_posting_counter_eq4(knn):
+    import torch
+    S = synth.spectrum_u8(20000, 111, role="S")
+    R = synth.spectrum_u8(100, 112, role="R")
+    want = refdefs.postings_touched_iib(R, S)
+    idx = knn.knn_join_build_index(S, block_size=2048)
+    counts = {}
+    for mode in ("iib", "iiib"):
+        c = torch.zeros(1, dtype=torch.int64, device="cuda")
+        # one group per row: every S block after the first carries the row's threshold
+        knn.knn_join(idx, knn.DeviceCSR.from_host(R), 5, mode=mode, postings_scanned=c, s_groups=1)
+        torch.cuda.synchronize()
+        counts[mode] = int(c.item())
+    assert counts["iib"] == want
+    assert counts["iiib"] < counts["iib"]
+    idx.close()
+
+
+# ----------------------------------------------------------------------------------
+# the benchmark's configuration at full size, on sampled rows
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.slow
+def test_config2_full_size_sampled_rows(knn, oracle_mod):
+    import torch
+    R, S, k = synth.config2()
+    idx = knn.knn_join_build_index(S)
+    ids, sc = knn.knn_join(idx, knn.DeviceCSR.from_host(R), k)
+    torch.cuda.synchronize()
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    rows = np.random.default_rng(7).choice(R.n_rows, size=48, replace=False)
+    rows.sort()
+    Rs = R.take_rows(rows)
+    eids, esc, _ = oracle_mod.iib_join(Rs, S, k, threads=0)
+    compare.assert_exact(ids[rows], sc[rows], eids, esc, "config2 full size")
+    idx.close()
