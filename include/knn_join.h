@@ -155,7 +155,23 @@ typedef struct {
     int32_t outputs_on_host;    /* 1: out_ids/out_scores are host pointers; the call then
                                    synchronises `stream` before returning                */
     int32_t skip_validation;    /* 1: trust R (sorted, in range, w > 0)                   */
+    float level_margin;         /* Section 4.4 cut per S block: the highest level l with
+                                   M * L_l <= level_margin * theta (0 = 1.0).  Lower values
+                                   scan more postings and complete fewer candidates.     */
+    int64_t* stats;             /* device int64[KNN_STATS_LEN] or NULL: work counters,
+                                   added to (see KNN_STAT_*)                              */
 } knn_join_opts;
+
+/* Work counters of knn_join (indices into knn_join_opts.stats). */
+#define KNN_STAT_BLOCK_STEPS 0      /* (row, S block) pairs processed                      */
+#define KNN_STAT_CANDIDATES 1       /* accumulator entries passing the level bound          */
+#define KNN_STAT_COMPLETED 2        /* entries completed over their unindexed features      */
+#define KNN_STAT_PUSHED 3           /* keys pushed to the top-k merge                       */
+#define KNN_STAT_MERGES 4           /* top-k merges                                         */
+#define KNN_STAT_ROUNDS 5           /* extra candidate rounds (push buffer full)            */
+#define KNN_STAT_RESIDUAL_FEATURES 6 /* unindexed features merged in completions            */
+#define KNN_STAT_POSTINGS 7         /* postings scanned                                     */
+#define KNN_STATS_LEN 8
 
 /* Exact top-k of every row of R against the indexed S.
  *   index       built by knn_join_build_index (same dim and dtype as R).
@@ -165,7 +181,7 @@ typedef struct {
  *   out_scores  int32 (KNN_U8) or float (KNN_F32) [n_rows * k], 0 padding.
  * Row i lists min(k, #{s : dot(r_i, s) > 0}) entries (with init_threshold: those with
  * dot >= init_threshold[i]) ordered by (score desc, id asc).
- * Synchronises `stream` unless skip_validation is set and R is on the device.
+ * Synchronises `stream` (it reads R's size and longest row back to size the launch).
  * Errors: KNN_EINVAL (bad R, dim/dtype mismatch, k < 1), KNN_EUNSUPPORTED (k > 64,
  * a row too long for one CTA's shared memory, u8 scores that could overflow int32),
  * KNN_ENOMEM, KNN_ECUDA.                                                           */

@@ -53,7 +53,11 @@ class _JoinOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("threads", ctypes.c_int32), ("s_groups", ctypes.c_int32),
                 ("init_threshold", ctypes.c_void_p), ("n_found", ctypes.c_void_p),
                 ("postings_scanned", ctypes.c_void_p), ("outputs_on_host", ctypes.c_int32),
-                ("skip_validation", ctypes.c_int32)]
+                ("skip_validation", ctypes.c_int32), ("level_margin", ctypes.c_float),
+                ("stats", ctypes.c_void_p)]
+
+KNN_STATS = ("block_steps", "candidates", "completed", "pushed", "merges", "rounds",
+             "residual_features", "postings")
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -237,7 +241,8 @@ def knn_join_build_index(S, block_size: int = 0, n_levels: int = 0, stream=None)
 def knn_join(index: Index, R, k: int, *, mode: str = "iiib", threads: int = 0, s_groups: int = 0,
              init_threshold: torch.Tensor | None = None, n_found: torch.Tensor | None = None,
              postings_scanned: torch.Tensor | None = None, out_ids=None, out_scores=None,
-             outputs_on_host: bool = False, skip_validation: bool = False, stream=None):
+             outputs_on_host: bool = False, skip_validation: bool = False, level_margin: float = 0.0,
+             stats: torch.Tensor | None = None, stream=None):
     """Exact top-k of every row of R; returns (ids, scores).
 
     Device outputs are torch tensors on the current device unless ``out_ids`` /
@@ -258,7 +263,8 @@ def knn_join(index: Index, R, k: int, *, mode: str = "iiib", threads: int = 0, s
             out_scores = torch.empty((n, k), dtype=sdt, device="cuda")
     opts = _JoinOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), int(s_groups),
                      _ptr(init_threshold), _ptr(n_found), _ptr(postings_scanned),
-                     int(bool(outputs_on_host)), int(bool(skip_validation)))
+                     int(bool(outputs_on_host)), int(bool(skip_validation)), float(level_margin),
+                     _ptr(stats))
     ip = out_ids.ctypes.data if isinstance(out_ids, np.ndarray) else out_ids.data_ptr()
     sp = out_scores.ctypes.data if isinstance(out_scores, np.ndarray) else out_scores.data_ptr()
     _check(L, L.knn_join(index.handle, ctypes.byref(c), int(k), ctypes.byref(opts), ip, sp,

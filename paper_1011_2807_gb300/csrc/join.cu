@@ -61,6 +61,18 @@ struct JT<uint8_t> {
         return (u64)(uint32_t)c << 32;
     }
     static constexpr double SLACK = 0.0;
+    // bound on the unindexed residual at a level: M * (largest integer weight sum <= L)
+    __device__ static double level_bound(double M, float L) { return M * floor((double)L); }
+    // smallest partial score whose upper bound (partial + lb) reaches theta
+    __device__ static int32_t cheap_min(double theta, double lb) {
+        double c = ceil(theta - lb);
+        if (c < 1.0) c = 1.0;
+        if (c > 2147483647.0) c = 2147483647.0;
+        return (int32_t)c;
+    }
+    __device__ static bool exact_ok(int32_t v, double M, uint32_t ub_bits, double theta) {
+        return (double)v + M * (double)ub_bits >= theta;
+    }
 };
 template <>
 struct JT<float> {
@@ -78,6 +90,15 @@ struct JT<float> {
     }
     // fp32 sums may differ from the real sum by a few ulps; widen bounds a little
     static constexpr double SLACK = 1.0 / (1 << 20);
+    __device__ static double level_bound(double M, float L) { return M * (double)L * (1.0 + SLACK); }
+    __device__ static float cheap_min(double theta, double lb) {
+        double c = (theta - lb) * (1.0 - SLACK);
+        if (c <= 0.0) return 0.0f;
+        return __double2float_rd(c);
+    }
+    __device__ static bool exact_ok(float v, double M, uint32_t ub_bits, double theta) {
+        return ((double)v + M * (double)__uint_as_float(ub_bits)) * (1.0 + SLACK) >= theta;
+    }
 };
 
 struct JoinParams {
@@ -96,6 +117,7 @@ struct JoinParams {
     const uint32_t* ubound;
     float levels[KNN_MAX_LEVELS];
     int32_t k, groups, blocks_per_group, iiib, max_r_nnz;
+    float level_margin;
     const float* init_thr;
     u64* part_keys;
     int32_t* out_ids;
@@ -103,6 +125,7 @@ struct JoinParams {
     int32_t* n_found;
     u64* floor_keys;
     unsigned long long* touched;
+    unsigned long long* stats;
 };
 
 struct SmemLayout {
@@ -243,7 +266,8 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     }
     __syncthreads();
 
-    unsigned long long touched = 0;
+    unsigned long long n_post = 0, n_cand = 0, n_comp = 0, n_push = 0, n_resf = 0;
+    unsigned long long n_steps = 0, n_merges = 0, n_rounds = 0;
     const int chunks = nb / (T * 4);  // <= 16 by construction (mask has 64 bits)
 
     for (int b = (rn > 0 ? b0 : b1); b < b1; b++) {
@@ -261,14 +285,15 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
             int level = 0;
             if (p.iiib) {
                 for (int l = p.n_levels - 1; l >= 1; l--) {
-                    double lim = st.M * (double)p.levels[l] * (1.0 + JT<W>::SLACK);
-                    if (lim < theta) {
+                    double lb = JT<W>::level_bound(st.M, p.levels[l]);
+                    if (lb < theta && lb <= p.level_margin * theta) {
                         level = l;
                         break;
                     }
                 }
             }
             st.level = level;
+            n_steps++;
         }
         __syncthreads();
         const int level = st.level;
@@ -288,7 +313,7 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
                 const uint32_t beg = lbeg[i], end = lend[i];
                 if (beg >= end) continue;
                 const Acc rw = rf_w[i];
-                touched += (lane == 0) ? (end - beg) : 0;
+                n_post += (lane == 0) ? (end - beg) : 0;
                 uint32_t q = (beg & ~(uint32_t)(V - 1)) + (uint32_t)lane * V;
                 for (; q < end; q += 32 * V * 2) {
                     uint4 v0 = *(const uint4*)(post + q);
@@ -313,9 +338,9 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
         }
         __syncthreads();
         // ---- 3. select ----
-        const double theta = st.theta;
         const double M = st.M;
-        const double lvl_bound = level > 0 ? M * (double)p.levels[level] : 0.0;
+        const double lb = level > 0 ? JT<W>::level_bound(M, p.levels[level]) : 0.0;
+        const Acc cmin = JT<W>::cheap_min(st.theta, lb);
         const int64_t gbase = (int64_t)b << p.block_shift;
         unsigned long long mask = 0ull;
         int mycount = 0;
@@ -325,12 +350,7 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
             Acc* v = (Acc*)&raw;
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                bool keep = false;
-                if (v[e] > (Acc)0) {
-                    double ub = ((double)v[e] + lvl_bound) * (1.0 + JT<W>::SLACK);
-                    keep = ub >= theta;
-                }
-                if (keep) {
+                if (v[e] > (Acc)0 && v[e] >= cmin) {
                     mask |= 1ull << (c * 4 + e);
                     mycount++;
                 } else {
@@ -339,7 +359,8 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
             }
             *(int4*)(acc + lid0) = raw;
         }
-        // total cheap candidates
+        n_cand += mycount;
+        // total candidates of the block
         int wsum = mycount;
         for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
         if (lane == 0) red_u[warp] = (unsigned long long)wsum;
@@ -356,8 +377,9 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
             int done_here = 0;
             const u64 kth = st.kth;
             const u64 fl = st.floor;
-            const double th = one_round ? theta
-                                        : fmax(theta, JT<W>::score_of_bits((uint32_t)((kth > fl ? kth : fl) >> 32)));
+            const double th = one_round ? st.theta
+                                        : fmax(st.theta, JT<W>::score_of_bits((uint32_t)((kth > fl ? kth : fl) >> 32)));
+            const Acc cm = one_round ? cmin : JT<W>::cheap_min(th, lb);
             while (mask && done_here < per_round) {
                 int bit = __ffsll(mask) - 1;
                 mask &= mask - 1;
@@ -367,15 +389,14 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
                 Acc v = acc[lid];
                 acc[lid] = (Acc)0;
                 int64_t gid = gbase + lid;
-                // cheap bound against the (possibly raised) threshold
-                if (((double)v + lvl_bound) * (1.0 + JT<W>::SLACK) < th) continue;
+                if (v < cm) continue;   // the threshold rose in an earlier round
                 Acc full = v;
                 if (level > 0) {
-                    double ub = ((double)v + M * JT<W>::ubound(p.ubound[(int64_t)level * p.n_s + gid])) *
-                                (1.0 + JT<W>::SLACK);
-                    if (ub < th) continue;
+                    if (!JT<W>::exact_ok(v, M, p.ubound[(int64_t)level * p.n_s + gid], th)) continue;
+                    n_comp++;
                     const int64_t j0 = p.s_indptr[gid];
                     const int m = p.n_unidx[(int64_t)level * p.n_s + gid];
+                    n_resf += m;
                     Acc res = (Acc)0;
                     for (int q = 0; q < m; q++) {
                         int32_t d = p.sp_d[j0 + q];
@@ -388,13 +409,13 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
                 if (key >= fl && key > kth) {
                     int slot = atomicAdd(&st.cnt, 1);
                     sortbuf[slot] = key;
+                    n_push++;
                 }
             }
-            if (one_round) {
-                merge_topk(topk, sortbuf, st, p.k);
-                break;
-            }
+            if (tid == 0 && st.cnt > 0) n_merges++;
             merge_topk(topk, sortbuf, st, p.k);
+            if (one_round) break;
+            if (tid == 0) n_rounds++;
             if (!__syncthreads_or(mask != 0ull)) break;
         }
         // publish this group's k-th key as a floor for the other groups of the row
@@ -415,10 +436,18 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
         for (int q = tid; q < p.k; q += T)
             p.part_keys[((int64_t)row * p.groups + g) * p.k + q] = q < st.size ? topk[q] : 0ull;
     }
-    // posting counter
-    if (p.touched) {
-        for (int o = 16; o > 0; o >>= 1) touched += __shfl_xor_sync(0xffffffffu, touched, o);
-        if (lane == 0 && touched) atomicAdd(p.touched, touched);
+    // counters
+    if (p.touched || p.stats) {
+        unsigned long long c[8] = {n_steps, n_cand, n_comp, n_push, n_merges, n_rounds, n_resf, n_post};
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            for (int o = 16; o > 0; o >>= 1) c[j] += __shfl_xor_sync(0xffffffffu, c[j], o);
+        if (lane == 0) {
+            if (p.touched && c[7]) atomicAdd(p.touched, c[7]);
+            if (p.stats)
+                for (int j = 0; j < 8; j++)
+                    if (c[j]) atomicAdd(p.stats + j, c[j]);
+        }
     }
 }
 
@@ -538,6 +567,9 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     p.out_scores = d_sc;
     p.n_found = o.n_found;
     p.touched = (unsigned long long*)o.postings_scanned;
+    p.stats = (unsigned long long*)o.stats;
+    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 1.0f;
+    if (!(p.level_margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     if (groups > 1) {
         KNN_TRY(tmp.get(&p.part_keys, (size_t)r.n_rows * groups * k));
         KNN_TRY(tmp.get(&p.floor_keys, (size_t)r.n_rows));
