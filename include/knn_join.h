@@ -144,7 +144,7 @@ typedef enum {
 
 typedef struct {
     knn_mode mode;
-    int32_t threads;            /* threads per CTA (128..1024, multiple of 32); 0 = auto */
+    int32_t threads;            /* threads per CTA (128..1024, multiple of 32); 0 = 512  */
     int32_t s_groups;           /* S-block groups scanned in parallel per row; 0 = auto  */
     const float* init_threshold;/* device float[n_rows] or NULL.  When given, row i keeps
                                    only vectors with score >= init_threshold[i] (a
@@ -156,10 +156,12 @@ typedef struct {
                                    synchronises `stream` before returning                */
     int32_t skip_validation;    /* 1: trust R (sorted, in range, w > 0)                   */
     float level_margin;         /* Section 4.4 cut per S block: the highest level l with
-                                   M * L_l <= level_margin * theta (0 = 1.0).  Lower values
+                                   M * L_l <= level_margin * theta (0 = 0.25).  Lower values
                                    scan more postings and complete fewer candidates.     */
     int64_t* stats;             /* device int64[KNN_STATS_LEN] or NULL: work counters,
                                    added to (see KNN_STAT_*)                              */
+    int32_t blocks_per_launch;  /* with one group per row: S blocks per kernel launch;
+                                   every launch covers all rows (0 = 4)                    */
 } knn_join_opts;
 
 /* Work counters of knn_join (indices into knn_join_opts.stats). */

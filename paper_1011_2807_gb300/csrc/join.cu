@@ -51,6 +51,7 @@ struct JT<uint8_t> {
     static constexpr int PER_VEC = 4;  // postings per 16-byte load
     __device__ static uint32_t score_bits(int32_t v) { return (uint32_t)v; }
     __device__ static double score_of_bits(uint32_t b) { return (double)b; }
+    __device__ static int32_t value_of_bits(uint32_t b) { return (int32_t)b; }
     __device__ static int32_t post_lid(uint32_t p) { return (int32_t)(p & 0xFFFFu); }
     __device__ static int32_t post_w(uint32_t p) { return (int32_t)(p >> 16); }
     __device__ static double ubound(uint32_t b) { return (double)b; }
@@ -73,6 +74,10 @@ struct JT<uint8_t> {
     __device__ static bool exact_ok(int32_t v, double M, uint32_t ub_bits, double theta) {
         return (double)v + M * (double)ub_bits >= theta;
     }
+    template <class S>
+    __device__ static void set_cmin(S& st, int32_t c) { st.cmin_i = c; }
+    template <class S>
+    __device__ static int32_t get_cmin(const S& st) { return st.cmin_i; }
 };
 template <>
 struct JT<float> {
@@ -81,6 +86,7 @@ struct JT<float> {
     static constexpr int PER_VEC = 2;
     __device__ static uint32_t score_bits(float v) { return __float_as_uint(v); }
     __device__ static double score_of_bits(uint32_t b) { return (double)__uint_as_float(b); }
+    __device__ static float value_of_bits(uint32_t b) { return __uint_as_float(b); }
     __device__ static int32_t post_lid(uint2 p) { return (int32_t)p.x; }
     __device__ static float post_w(uint2 p) { return __uint_as_float(p.y); }
     __device__ static double ubound(uint32_t b) { return (double)__uint_as_float(b); }
@@ -93,12 +99,16 @@ struct JT<float> {
     __device__ static double level_bound(double M, float L) { return M * (double)L * (1.0 + SLACK); }
     __device__ static float cheap_min(double theta, double lb) {
         double c = (theta - lb) * (1.0 - SLACK);
-        if (c <= 0.0) return 0.0f;
-        return __double2float_rd(c);
+        float f = c > 0.0 ? __double2float_rd(c) : 0.0f;
+        return fmaxf(f, 1.40129846e-45f);   // candidates are always > 0
     }
     __device__ static bool exact_ok(float v, double M, uint32_t ub_bits, double theta) {
         return ((double)v + M * (double)__uint_as_float(ub_bits)) * (1.0 + SLACK) >= theta;
     }
+    template <class S>
+    __device__ static void set_cmin(S& st, float c) { st.cmin_f = c; }
+    template <class S>
+    __device__ static float get_cmin(const S& st) { return st.cmin_f; }
 };
 
 struct JoinParams {
@@ -126,10 +136,14 @@ struct JoinParams {
     u64* floor_keys;
     unsigned long long* touched;
     unsigned long long* stats;
+    // S-block-synchronous schedule (groups == 1): this launch covers blocks
+    // [block_begin, block_end) of every row; rows carry their top-k keys between launches
+    int32_t block_begin, block_end, carry_in, carry_out;
+    u64* carry;
 };
 
 struct SmemLayout {
-    size_t acc, rf_d, rf_w, lbeg, lend, topk, sort, total;
+    size_t acc, rf_d, rf_w, lbeg, lend, ipre, topk, sort, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -140,8 +154,9 @@ __host__ __device__ inline SmemLayout smem_layout(int nb, int max_r_nnz) {
     L.acc = o;  o = align16(o + (size_t)nb * 4);
     L.rf_d = o; o = align16(o + (size_t)max_r_nnz * 4);
     L.rf_w = o; o = align16(o + (size_t)max_r_nnz * 4);
-    L.lbeg = o; o = align16(o + (size_t)max_r_nnz * 4);
-    L.lend = o; o = align16(o + (size_t)max_r_nnz * 4);
+    L.lbeg = o; o = align16(o + (size_t)max_r_nnz * 8);   // two buffers (this / next S block)
+    L.lend = o; o = align16(o + (size_t)max_r_nnz * 8);
+    L.ipre = o; o = align16(o + (size_t)(max_r_nnz + 1) * 4);
     L.topk = o; o = align16(o + (size_t)KMAX * 8);
     L.sort = o; o = align16(o + (size_t)SORT_CAP * 8);
     L.total = o;
@@ -176,6 +191,17 @@ struct CtaState {
     u64 floor;      // keys below this never qualify
     u64 kth;        // current k-th key (0 while fewer than k)
     double M;       // largest weight of r
+    double lb;      // residual bound of the current level (0 at level 0)
+    float cmin_f;   // smallest partial score worth a look in this block (as float/int)
+    int32_t cmin_i;
+    double lbnd[KNN_MAX_LEVELS];  // residual bound of every level for this row
+    unsigned long long n_steps, n_merges, n_rounds;  // work counters (thread 0)
+    int next_list;  // next list of r to hand to a warp in the scan
+    int pred_level; // level the next block's list ranges were prefetched for (-1: none)
+    // radix select of a candidate threshold (blocks with too many candidates)
+    int rs_shift, rs_need, rs_done;
+    unsigned rs_prefix, rs_above, rs_key;
+    unsigned hist[256];
 };
 
 // merge pushed keys with topk; all threads
@@ -202,6 +228,75 @@ __device__ void merge_topk(u64* topk, u64* sortbuf, CtaState& st, int k) {
     __syncthreads();
 }
 
+// In-place exclusive scan of data[0..n) by the whole CTA; data[n] = total.
+// Each thread owns a contiguous segment; `wtot` holds 32 words of scratch.
+__device__ void cta_exclusive_scan(uint32_t* data, int n, uint32_t* wtot) {
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (n + T - 1) / T;
+    const int a = min(n, tid * per), b = min(n, a + per);
+    uint32_t s = 0;
+    for (int i = a; i < b; i++) s += data[i];
+    uint32_t x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wtot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < (T >> 5) ? wtot[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < (T >> 5)) wtot[lane] = t;   // inclusive warp totals
+    }
+    __syncthreads();
+    uint32_t run = (warp ? wtot[warp - 1] : 0u) + x - s;
+    for (int i = a; i < b; i++) {
+        uint32_t v = data[i];
+        data[i] = run;
+        run += v;
+    }
+    if (tid == T - 1) data[n] = wtot[(T >> 5) - 1];
+    __syncthreads();
+}
+
+// Shared-memory accesses through 32-bit shared addresses (no generic-address checks).
+__device__ __forceinline__ void red_add_shared(uint32_t saddr, int32_t v) {
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(saddr), "r"(v));
+}
+__device__ __forceinline__ void red_add_shared(uint32_t saddr, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(saddr), "f"(v));
+}
+__device__ __forceinline__ int4 ld_shared_v4(uint32_t saddr) {
+    int4 r;
+    asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "r"(saddr));
+    return r;
+}
+__device__ __forceinline__ void st_shared_v4(uint32_t saddr, int4 v) {
+    asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(saddr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void prefetch_l1(const void* ptr) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(ptr));
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* ptr) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
 template <class W>
 __device__ __forceinline__ typename JT<W>::Acc lookup_r(const int32_t* rf_d, const typename JT<W>::Acc* rf_w,
                                                         int n, int32_t d) {
@@ -226,10 +321,12 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     const int nb = 1 << p.block_shift;
     const SmemLayout L = smem_layout(nb, p.max_r_nnz);
     Acc* acc = (Acc*)(smem + L.acc);
+    const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
     int32_t* rf_d = (int32_t*)(smem + L.rf_d);
     Acc* rf_w = (Acc*)(smem + L.rf_w);
-    uint32_t* lbeg = (uint32_t*)(smem + L.lbeg);
-    uint32_t* lend = (uint32_t*)(smem + L.lend);
+    uint32_t* lbeg_buf = (uint32_t*)(smem + L.lbeg);
+    uint32_t* lend_buf = (uint32_t*)(smem + L.lend);
+    uint32_t* ipre = (uint32_t*)(smem + L.ipre);
     u64* topk = (u64*)(smem + L.topk);
     u64* sortbuf = (u64*)(smem + L.sort);
 
@@ -239,8 +336,8 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     const int g = blockIdx.x - (int)(row * p.groups);
     const int64_t ra = p.r_indptr[row];
     const int rn = (int)(p.r_indptr[row + 1] - ra);
-    const int b0 = g * p.blocks_per_group;
-    const int b1 = min(p.n_blocks, b0 + p.blocks_per_group);
+    const int b0 = p.groups == 1 ? p.block_begin : g * p.blocks_per_group;
+    const int b1 = p.groups == 1 ? p.block_end : min(p.n_blocks, b0 + p.blocks_per_group);
 
     // load r (ascending d) and its largest weight
     double mloc = 0.0;
@@ -263,75 +360,138 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
         st.cnt = 0;
         st.kth = 0ull;
         st.floor = p.init_thr ? JT<W>::floor_key(p.init_thr[row]) : ((u64)1 << 32);
+        st.n_steps = st.n_merges = st.n_rounds = 0;
+        st.pred_level = -1;
+        for (int l = 0; l < p.n_levels; l++) st.lbnd[l] = l ? JT<W>::level_bound(m, p.levels[l]) : 0.0;
+    }
+    if (p.carry_in) {   // the row's top-k from the blocks of earlier launches
+        for (int q = tid; q < p.k; q += T) topk[q] = p.carry[row * p.k + q];
+        __syncthreads();
+        if (tid == 0) {
+            int n = 0;
+            while (n < p.k && topk[n] != 0ull) n++;
+            st.size = n;
+            st.kth = n == p.k ? topk[p.k - 1] : 0ull;
+        }
     }
     __syncthreads();
 
-    unsigned long long n_post = 0, n_cand = 0, n_comp = 0, n_push = 0, n_resf = 0;
-    unsigned long long n_steps = 0, n_merges = 0, n_rounds = 0;
+    uint32_t n_cand = 0, n_comp = 0, n_push = 0, n_resf = 0;   // this thread's counters
+    unsigned long long n_post = 0;                              // postings (sub-warp leaders)
     const int chunks = nb / (T * 4);  // <= 16 by construction (mask has 64 bits)
 
     for (int b = (rn > 0 ? b0 : b1); b < b1; b++) {
-        // ---- 1. threshold and level ----
-        if (tid == 0) {
+        // ---- 1. threshold and level (warp 0: lane l tests level l) ----
+        if (warp == 0) {
             u64 fl = st.floor;
             if (p.floor_keys) {
                 u64 shared = *(volatile u64*)(p.floor_keys + row);
                 if (shared > fl) fl = shared;
             }
-            st.floor = fl;
-            u64 eff = st.kth > fl ? st.kth : fl;
-            double theta = JT<W>::score_of_bits((uint32_t)(eff >> 32));
-            st.theta = theta;
-            int level = 0;
-            if (p.iiib) {
-                for (int l = p.n_levels - 1; l >= 1; l--) {
-                    double lb = JT<W>::level_bound(st.M, p.levels[l]);
-                    if (lb < theta && lb <= p.level_margin * theta) {
-                        level = l;
-                        break;
-                    }
-                }
+            const u64 eff = st.kth > fl ? st.kth : fl;
+            const double theta = JT<W>::score_of_bits((uint32_t)(eff >> 32));
+            bool ok = false;
+            if (p.iiib && lane >= 1 && lane < p.n_levels) {
+                const double lb = st.lbnd[lane];
+                ok = lb < theta && lb <= p.level_margin * theta;
             }
-            st.level = level;
-            n_steps++;
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0) {
+                const int level = m ? 31 - __clz(m) : 0;
+                st.next_list = nwarps;   // list counter of this block's scan
+                st.floor = fl;
+                st.theta = theta;
+                st.level = level;
+                st.n_steps++;
+                st.lb = st.lbnd[level];
+                JT<W>::set_cmin(st, JT<W>::cheap_min(theta, st.lb));
+            }
         }
         __syncthreads();
         const int level = st.level;
         // ---- list ranges of r's features in block b at this level ----
-        const size_t bbase = (size_t)b * (size_t)p.dim;
-        for (int i = tid; i < rn; i += T) {
-            size_t base = (bbase + (size_t)rf_d[i]) * (size_t)p.n_levels;
-            lbeg[i] = p.binoff[base];
-            lend[i] = p.binoff[base + (size_t)(p.n_levels - level)];
+        // They were requested (cp.async) during the previous block's scan for the level
+        // that block used; if the level changed, or this is the first block, load now.
+        constexpr int V = JT<W>::PER_VEC;   // postings per 16-byte chunk
+        uint32_t* lbeg = lbeg_buf + (b & 1) * p.max_r_nnz;
+        uint32_t* lend = lend_buf + (b & 1) * p.max_r_nnz;
+        const int pred = st.pred_level;
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (pred != level) {
+            const size_t bbase = (size_t)b * (size_t)p.dim;
+            for (int i = tid; i < rn; i += T) {
+                size_t base = (bbase + (size_t)rf_d[i]) * (size_t)p.n_levels;
+                lbeg[i] = p.binoff[base];
+                lend[i] = p.binoff[base + (size_t)(p.n_levels - level)];
+            }
         }
         __syncthreads();
+        if (tid == 0) st.pred_level = b + 1 < b1 ? level : -1;   // read before the barrier above
+        if (b + 1 < b1) {   // next block's ranges, assuming the level stays
+            uint32_t* nbeg = lbeg_buf + ((b + 1) & 1) * p.max_r_nnz;
+            uint32_t* nend = lend_buf + ((b + 1) & 1) * p.max_r_nnz;
+            const size_t nbase = (size_t)(b + 1) * (size_t)p.dim;
+            for (int i = tid; i < rn; i += T) {
+                size_t base = (nbase + (size_t)rf_d[i]) * (size_t)p.n_levels;
+                cp_async4(nbeg + i, p.binoff + base);
+                cp_async4(nend + i, p.binoff + base + (size_t)(p.n_levels - level));
+            }
+            cp_async_commit();
+        }
         // ---- 2. scan: acc[lid] += r[d] * w over the indexed prefixes ----
+        // The lists' 16-byte chunks are cut into work items of at most CH chunks (an item
+        // never spans two lists).  Each 8-lane sub-warp takes an equal contiguous range
+        // of items, so every sub-warp runs the same number of iterations; per item each
+        // lane loads U chunks (one 128-byte line per sub-warp per load) before adding.
         {
+            constexpr int G = 8, U = 4, CH = G * U;
+            for (int i = tid; i < rn; i += T) {
+                const uint32_t bg = lbeg[i], en = lend[i];
+                const uint32_t nch = en > bg ? (en + V - 1) / V - bg / V : 0u;
+                ipre[i] = (nch + CH - 1) / CH;
+            }
+            __syncthreads();
+            cta_exclusive_scan(ipre, rn, (uint32_t*)red_u);
             const Post* post = (const Post*)p.postings;
-            constexpr int V = JT<W>::PER_VEC;
-            for (int i = warp; i < rn; i += nwarps) {
-                const uint32_t beg = lbeg[i], end = lend[i];
-                if (beg >= end) continue;
-                const Acc rw = rf_w[i];
-                n_post += (lane == 0) ? (end - beg) : 0;
-                uint32_t q = (beg & ~(uint32_t)(V - 1)) + (uint32_t)lane * V;
-                for (; q < end; q += 32 * V * 2) {
-                    uint4 v0 = *(const uint4*)(post + q);
-                    uint32_t q1 = q + 32 * V;
-                    uint4 v1 = make_uint4(0, 0, 0, 0);
-                    if (q1 < end) v1 = *(const uint4*)(post + q1);
-                    const Post* e0 = (const Post*)&v0;
-                    const Post* e1 = (const Post*)&v1;
+            const int nsub = T / G, sub = tid / G, sl = tid % G;
+            const uint32_t total = ipre[rn];
+            const uint32_t per = (total + nsub - 1) / nsub;
+            const uint32_t I0 = min(total, (uint32_t)sub * per), I1 = min(total, I0 + per);
+            int li = 0;
+            {   // largest li with ipre[li] <= I0
+                int lo = 0, hi = rn;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (ipre[mid] <= I0) lo = mid;
+                    else hi = mid - 1;
+                }
+                li = lo;
+            }
+            for (uint32_t I = I0; I < I1; I++) {
+                while (ipre[li + 1] <= I) li++;
+                const uint32_t bg = lbeg[li], en = lend[li];
+                const Acc rw = rf_w[li];
+                const uint32_t cf = bg / V, cend = (en + V - 1) / V;
+                const uint32_t c0 = cf + (I - ipre[li]) * CH;
+                const uint32_t c1 = min(cend, c0 + CH);
+                if (sl == 0) n_post += min(c1 * V, en) - max(c0 * V, bg);
+                uint4 v[U];
 #pragma unroll
-                    for (int e = 0; e < V; e++) {
-                        uint32_t pe = q + e;
-                        if (pe >= beg && pe < end)
-                            atomicAdd(&acc[JT<W>::post_lid(e0[e])], rw * JT<W>::post_w(e0[e]));
-                    }
+                for (int u = 0; u < U; u++) {
+                    const uint32_t c = c0 + sl + G * u;
+                    if (c < c1) v[u] = *(const uint4*)(post + (size_t)c * V);
+                }
 #pragma unroll
-                    for (int e = 0; e < V; e++) {
-                        uint32_t pe = q1 + e;
-                        if (pe < end) atomicAdd(&acc[JT<W>::post_lid(e1[e])], rw * JT<W>::post_w(e1[e]));
+                for (int u = 0; u < U; u++) {
+                    const uint32_t c = c0 + sl + G * u;
+                    if (c < c1) {
+                        const Post* e = (const Post*)&v[u];
+                        const uint32_t p0 = c * V;
+#pragma unroll
+                        for (int j = 0; j < V; j++) {
+                            if (p0 + j >= bg && p0 + j < en)
+                                red_add_shared(acc_s + 4u * (uint32_t)JT<W>::post_lid(e[j]), rw * JT<W>::post_w(e[j]));
+                        }
                     }
                 }
             }
@@ -339,25 +499,29 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
         __syncthreads();
         // ---- 3. select ----
         const double M = st.M;
-        const double lb = level > 0 ? JT<W>::level_bound(M, p.levels[level]) : 0.0;
-        const Acc cmin = JT<W>::cheap_min(st.theta, lb);
+        const double lb = st.lb;
+        const Acc cmin = JT<W>::get_cmin(st);   // > 0
         const int64_t gbase = (int64_t)b << p.block_shift;
         unsigned long long mask = 0ull;
         int mycount = 0;
         for (int c = 0; c < chunks; c++) {
             int lid0 = c * T * 4 + tid * 4;
-            int4 raw = *(int4*)(acc + lid0);
+            int4 raw = ld_shared_v4(acc_s + 4u * lid0);
             Acc* v = (Acc*)&raw;
+            if (v[0] < cmin && v[1] < cmin && v[2] < cmin && v[3] < cmin) {
+                st_shared_v4(acc_s + 4u * lid0, make_int4(0, 0, 0, 0));
+                continue;
+            }
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                if (v[e] > (Acc)0 && v[e] >= cmin) {
+                if (v[e] >= cmin) {
                     mask |= 1ull << (c * 4 + e);
                     mycount++;
                 } else {
                     v[e] = (Acc)0;
                 }
             }
-            *(int4*)(acc + lid0) = raw;
+            st_shared_v4(acc_s + 4u * lid0, raw);
         }
         n_cand += mycount;
         // total candidates of the block
@@ -371,6 +535,96 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
             st.pending = (int)t;
         }
         __syncthreads();
+        if (st.pending > PUSH_CAP) {
+            // Too many candidates for one merge (typically the first block, where the
+            // threshold is still 0).  Radix-select, on the candidates' partial scores,
+            // a value t with at least k candidates >= t and at most PUSH_CAP of them;
+            // then a candidate whose full score is below t (partial < t - lb) cannot
+            // reach the row's top-k: k entries of this block already beat it.
+            unsigned kmax_l = 0;
+            for (unsigned long long mm = mask; mm; mm &= mm - 1) {
+                int bit = __ffsll(mm) - 1;
+                int lid = (bit >> 2) * T * 4 + tid * 4 + (bit & 3);
+                kmax_l = max(kmax_l, JT<W>::score_bits(acc[lid]));
+            }
+            for (int o = 16; o > 0; o >>= 1) kmax_l = max(kmax_l, __shfl_xor_sync(0xffffffffu, kmax_l, o));
+            if (lane == 0) red_u[warp] = kmax_l;
+            __syncthreads();
+            if (tid == 0) {
+                unsigned km = 0;
+                for (int w = 0; w < nwarps; w++) km = max(km, (unsigned)red_u[w]);
+                const unsigned kmin = JT<W>::score_bits(cmin);
+                const unsigned diff = km ^ kmin;
+                const int hb = diff ? 31 - __clz(diff) : 0;
+                st.rs_shift = hb + 1;     // lowest bit already fixed in the prefix
+                st.rs_prefix = hb >= 31 ? 0u : (km & ~((2u << hb) - 1u));
+                st.rs_need = p.k;
+                st.rs_above = 0;
+                st.rs_done = diff == 0;   // all candidates equal: nothing to split
+                st.rs_key = kmin;
+            }
+            __syncthreads();
+            while (!st.rs_done) {
+                const int lo = st.rs_shift;                 // bits >= lo are fixed
+                const int shift = lo > 8 ? lo - 8 : 0;      // this pass: bits [shift, lo)
+                const unsigned dmask = (1u << (lo - shift)) - 1u;
+                const unsigned prefix = st.rs_prefix;
+                const unsigned hi_mask = lo >= 32 ? 0u : ~((1u << lo) - 1u);
+                for (int i = tid; i < 256; i += T) st.hist[i] = 0;
+                __syncthreads();
+                for (unsigned long long mm = mask; mm; mm &= mm - 1) {
+                    int bit = __ffsll(mm) - 1;
+                    int lid = (bit >> 2) * T * 4 + tid * 4 + (bit & 3);
+                    unsigned key = JT<W>::score_bits(acc[lid]);
+                    if ((key & hi_mask) == (prefix & hi_mask)) atomicAdd(&st.hist[(key >> shift) & dmask], 1u);
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    unsigned above = 0;
+                    int t = (int)dmask;
+                    for (; t > 0; t--) {
+                        if (above + st.hist[t] >= (unsigned)st.rs_need) break;
+                        above += st.hist[t];
+                    }
+                    const unsigned newprefix = (prefix & hi_mask) | ((unsigned)t << shift);
+                    const unsigned total = st.rs_above + above + st.hist[t];
+                    if (total <= (unsigned)PUSH_CAP || shift == 0) {
+                        st.rs_key = newprefix;
+                        st.rs_done = 1;
+                    } else {
+                        st.rs_prefix = newprefix;
+                        st.rs_need -= (int)above;
+                        st.rs_above += above;
+                        st.rs_shift = shift;
+                    }
+                }
+                __syncthreads();
+            }
+            // drop candidates below the selected value
+            const double tv = (double)JT<W>::value_of_bits(st.rs_key);
+            const Acc c2 = JT<W>::cheap_min(tv, lb);
+            int kept = 0;
+            for (unsigned long long mm = mask; mm; mm &= mm - 1) {
+                int bit = __ffsll(mm) - 1;
+                int lid = (bit >> 2) * T * 4 + tid * 4 + (bit & 3);
+                if (acc[lid] < c2) {
+                    acc[lid] = (Acc)0;
+                    mask &= ~(1ull << bit);
+                } else {
+                    kept++;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+            __syncthreads();
+            if (lane == 0) red_u[warp] = (unsigned long long)kept;
+            __syncthreads();
+            if (tid == 0) {
+                unsigned long long t = 0;
+                for (int w = 0; w < nwarps; w++) t += red_u[w];
+                st.pending = (int)t;
+            }
+            __syncthreads();
+        }
         const bool one_round = st.pending <= PUSH_CAP;
         const int per_round = one_round ? 64 : max(1, PUSH_CAP / T);
         while (true) {
@@ -412,10 +666,10 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
                     n_push++;
                 }
             }
-            if (tid == 0 && st.cnt > 0) n_merges++;
+            if (tid == 0 && st.cnt > 0) st.n_merges++;
             merge_topk(topk, sortbuf, st, p.k);
             if (one_round) break;
-            if (tid == 0) n_rounds++;
+            if (tid == 0) st.n_rounds++;
             if (!__syncthreads_or(mask != 0ull)) break;
         }
         // publish this group's k-th key as a floor for the other groups of the row
@@ -424,7 +678,9 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     }
 
     // ---- output ----
-    if (p.groups == 1) {
+    if (p.carry_out) {
+        for (int q = tid; q < p.k; q += T) p.carry[row * p.k + q] = q < st.size ? topk[q] : 0ull;
+    } else if (p.groups == 1) {
         for (int q = tid; q < p.k; q += T) {
             u64 key = q < st.size ? topk[q] : 0ull;
             int64_t o = row * p.k + q;
@@ -438,7 +694,9 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     }
     // counters
     if (p.touched || p.stats) {
-        unsigned long long c[8] = {n_steps, n_cand, n_comp, n_push, n_merges, n_rounds, n_resf, n_post};
+        const bool t0 = tid == 0;
+        unsigned long long c[8] = {t0 ? st.n_steps : 0ull, n_cand, n_comp, n_push, t0 ? st.n_merges : 0ull,
+                                   t0 ? st.n_rounds : 0ull, n_resf, n_post};
 #pragma unroll
         for (int j = 0; j < 8; j++)
             for (int o = 16; o > 0; o >>= 1) c[j] += __shfl_xor_sync(0xffffffffu, c[j], o);
@@ -499,7 +757,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
         if (bound >= 2147483647.0) return fail(KNN_EUNSUPPORTED, "uint8 scores could overflow int32");
     }
     const int nb = ix->block_size;
-    int T = o.threads ? o.threads : 256;
+    int T = o.threads ? o.threads : 512;
     if (T < 128 || T > 1024 || (T & 31)) return fail(KNN_EINVAL, "threads must be a multiple of 32 in [128, 1024]");
     // each thread owns 4 accumulator entries per chunk and a 64-bit candidate mask:
     // T * 4 <= nb and nb / (T * 4) <= 16 (nb and T are powers of two times 32)
@@ -568,7 +826,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     p.n_found = o.n_found;
     p.touched = (unsigned long long*)o.postings_scanned;
     p.stats = (unsigned long long*)o.stats;
-    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 1.0f;
+    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 0.25f;
     if (!(p.level_margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     if (groups > 1) {
         KNN_TRY(tmp.get(&p.part_keys, (size_t)r.n_rows * groups * k));
@@ -576,15 +834,28 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
         KNN_CUDA_TRY(cudaMemsetAsync(p.floor_keys, 0, sizeof(u64) * r.n_rows, stream));
     }
     int64_t grid = r.n_rows * groups;
-    if (ix->dtype == KNN_U8) {
+    if (ix->dtype == KNN_U8)
         KNN_CUDA_TRY(cudaFuncSetAttribute(k_join<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-        k_join<uint8_t><<<(unsigned)grid, T, L.total, stream>>>(p);
-    } else {
+    else
         KNN_CUDA_TRY(cudaFuncSetAttribute(k_join<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-        k_join<float><<<(unsigned)grid, T, L.total, stream>>>(p);
+    // One group per row: S-block-synchronous launches.  Every launch walks all rows over
+    // the same few S blocks, so their postings stay in L2 while all rows read them.
+    int per_launch = groups == 1 ? (o.blocks_per_launch > 0 ? o.blocks_per_launch : 4) : ix->n_blocks;
+    per_launch = std::min(per_launch, ix->n_blocks);
+    const int n_launch = groups == 1 ? (int)ceil_div(ix->n_blocks, per_launch) : 1;
+    if (n_launch > 1) KNN_TRY(tmp.get(&p.carry, (size_t)r.n_rows * k));
+    for (int li = 0; li < n_launch; li++) {
+        p.block_begin = li * per_launch;
+        p.block_end = std::min(ix->n_blocks, (li + 1) * per_launch);
+        p.carry_in = li > 0;
+        p.carry_out = li + 1 < n_launch;
+        if (ix->dtype == KNN_U8)
+            k_join<uint8_t><<<(unsigned)grid, T, L.total, stream>>>(p);
+        else
+            k_join<float><<<(unsigned)grid, T, L.total, stream>>>(p);
+        KNN_CUDA_TRY(cudaGetLastError());
+        count_launch();
     }
-    KNN_CUDA_TRY(cudaGetLastError());
-    count_launch();
     if (groups > 1) {
         int P = 2;
         while (P < groups * k) P <<= 1;

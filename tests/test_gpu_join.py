@@ -90,6 +90,17 @@ def test_s_groups(knn, oracle_mod, groups):
     compare.assert_exact(ids, sc, eids, esc, f"groups={groups}")
 
 
+@pytest.mark.parametrize("bpl", [1, 3, 7, 100])
+@pytest.mark.parametrize("mode", ["iib", "iiib"])
+def test_block_synchronous_launches(knn, oracle_mod, bpl, mode):
+    # one group per row: rows carry their top-k across launches of bpl S blocks
+    S = synth.spectrum_u8(5000, 131, role="S")      # 20 blocks of 256
+    R = synth.spectrum_u8(90, 132, role="R")
+    eids, esc, _ = oracle_mod.iib_join(R, S, 7, threads=8)
+    ids, sc = run(knn, S, R, 7, mode=mode, block_size=256, s_groups=1, blocks_per_launch=bpl)
+    compare.assert_exact(ids, sc, eids, esc, f"bpl={bpl} {mode}")
+
+
 @pytest.mark.parametrize("threads", [128, 256, 512, 1024])
 def test_threads(knn, oracle_mod, threads):
     S = synth.spectrum_u8(6000, 51, role="S")
