@@ -840,7 +840,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
         KNN_CUDA_TRY(cudaFuncSetAttribute(k_join<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     // One group per row: S-block-synchronous launches.  Every launch walks all rows over
     // the same few S blocks, so their postings stay in L2 while all rows read them.
-    int per_launch = groups == 1 ? (o.blocks_per_launch > 0 ? o.blocks_per_launch : 4) : ix->n_blocks;
+    int per_launch = groups == 1 ? (o.blocks_per_launch > 0 ? o.blocks_per_launch : 8) : ix->n_blocks;
     per_launch = std::min(per_launch, ix->n_blocks);
     const int n_launch = groups == 1 ? (int)ceil_div(ix->n_blocks, per_launch) : 1;
     if (n_launch > 1) KNN_TRY(tmp.get(&p.carry, (size_t)r.n_rows * k));
