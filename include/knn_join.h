@@ -191,6 +191,35 @@ knn_status knn_join(const knn_index* index, const knn_csr* R, int32_t k,
                     const knn_join_opts* opts, int32_t* out_ids, void* out_scores,
                     void* stream);
 
+/* ------------------------------------------------------------------------------ */
+/* Allocation-free join.  The paper has no counterpart: this is an engineering      */
+/* variant of knn_join for callers that cannot let a library allocate device memory */
+/* during a call -- e.g. a server that has split the GPU between its own fixed      */
+/* pools, or a latency-critical loop that must not pay for an allocation or for the */
+/* device-wide synchronisation a free can cause.                                    */
+/* ------------------------------------------------------------------------------ */
+
+/* Size of the one scratch array (a file-scope __device__ array) the call works in.
+ * Every GPU that loads the library holds it until the process exits.               */
+#define KNN_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Same result, arguments and errors as knn_join, with these differences:
+ *   - allocates nothing: no cudaMalloc/cudaFree and no allocator-hook call; the
+ *     scratch (a check record of R and the top-k keys each row carries between
+ *     S-block launches) is the library's fixed array;
+ *   - R must be in device memory, outputs are device memory (outputs_on_host = 0);
+ *   - rows are always scanned with one S-block group per row (s_groups is ignored);
+ *   - n_rows * k must not exceed (KNN_NOALLOC_SCRATCH_BYTES - 256) / 8 = 2,097,120,
+ *     else KNN_EUNSUPPORTED with a message naming the limit.
+ * The first call on a device (with that device current) looks up the array's device
+ * address with cudaGetSymbolAddress; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents: calls that overlap
+ * on the GPU (other streams or host threads) race on it and must be serialised by the
+ * caller.  Synchronises `stream` (it reads R's size and longest row back).          */
+knn_status knn_join_noalloc(const knn_index* index, const knn_csr* R, int32_t k,
+                            const knn_join_opts* opts, int32_t* out_ids, void* out_scores,
+                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif

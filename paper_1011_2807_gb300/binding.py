@@ -100,6 +100,8 @@ def lib():
         L.knn_index_destroy.restype = None
         L.knn_join.argtypes = [ctypes.c_void_p, P(_Csr), ctypes.c_int32, P(_JoinOpts),
                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.knn_join_noalloc.argtypes = [ctypes.c_void_p, P(_Csr), ctypes.c_int32, P(_JoinOpts),
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         _alloc_cbs = (_ALLOC_FN(_torch_alloc), _FREE_FN(_torch_free))
         _check(L, L.knn_set_allocator(_alloc_cbs[0], _alloc_cbs[1], None))
         _lib = L
@@ -269,4 +271,29 @@ def knn_join(index: Index, R, k: int, *, mode: str = "iiib", threads: int = 0, s
     sp = out_scores.ctypes.data if isinstance(out_scores, np.ndarray) else out_scores.data_ptr()
     _check(L, L.knn_join(index.handle, ctypes.byref(c), int(k), ctypes.byref(opts), ip, sp,
                          _stream_ptr(stream)))
+    return out_ids, out_scores
+
+
+def knn_join_noalloc(index: Index, R: DeviceCSR, k: int, out_ids: torch.Tensor, out_scores: torch.Tensor, *,
+                     mode: str = "iiib", threads: int = 0, init_threshold: torch.Tensor | None = None,
+                     n_found: torch.Tensor | None = None, skip_validation: bool = False,
+                     level_margin: float = 0.0, blocks_per_launch: int = 0, stream=None):
+    """knn_join without any device allocation by the library.
+
+    For callers that cannot let a library allocate device memory during a call (a
+    process that has split the GPU between its own fixed pools, or a latency-critical
+    loop).  R and both outputs must already be in device memory; the library works in
+    its own fixed scratch array, so n_rows * k is limited (see include/knn_join.h) and
+    calls whose GPU work overlaps must be serialised by the caller.
+    """
+    L = lib()
+    if not isinstance(R, DeviceCSR) or not R.indptr.is_cuda:
+        raise TypeError("knn_join_noalloc needs a DeviceCSR on the GPU")
+    keep = []
+    c = _csr(R, keep)
+    opts = _JoinOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), 1,
+                     _ptr(init_threshold), _ptr(n_found), None, 0, int(bool(skip_validation)),
+                     float(level_margin), None, int(blocks_per_launch))
+    _check(L, L.knn_join_noalloc(index.handle, ctypes.byref(c), int(k), ctypes.byref(opts),
+                                 out_ids.data_ptr(), out_scores.data_ptr(), _stream_ptr(stream)))
     return out_ids, out_scores

@@ -97,6 +97,11 @@ struct DevCSR {
 knn_status prepare_csr(const knn_csr* in, cudaStream_t stream, Buffers& bufs, bool validate,
                        bool need_stats, DevCSR* out);
 
+// Same checks and statistics for a device CSR, with the check record placed in the
+// given device scratch (>= 256 bytes) instead of an allocation.
+knn_status check_device_csr_into(const knn_csr* in, void* scratch, bool validate, cudaStream_t stream,
+                                 DevCSR* out);
+
 // ---------------------------------------------------------------------------------
 // the index (owned device buffers + layout parameters)
 // ---------------------------------------------------------------------------------

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -869,6 +870,155 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
         KNN_CUDA_TRY(cudaMemcpyAsync(out_ids, d_ids, sizeof(int32_t) * r.n_rows * k, cudaMemcpyDeviceToHost, stream));
         KNN_CUDA_TRY(cudaMemcpyAsync(out_scores, d_sc, sizeof(uint32_t) * r.n_rows * k, cudaMemcpyDeviceToHost, stream));
         KNN_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
+    return KNN_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// knn_join_noalloc: the join for callers that must not allocate device memory
+//
+// Some callers cannot have a library allocate device memory while they run: a server
+// that has split the whole GPU between its own fixed pools and would see a foreign
+// allocation fail or fragment them, or a latency-critical loop where an allocation (or
+// the device-wide synchronisation that freeing memory can cause) is not acceptable.
+// This entry point runs the same k_join kernel as knn_join, but its scratch -- the
+// per-row check record and the top-k keys each row carries from one S-block launch to
+// the next -- lives in one file-scope __device__ array of KNN_NOALLOC_SCRATCH_BYTES.
+// Every GPU that loads this library holds that array until the process exits.
+//
+// Set-up: the first call on a device (with that device current) looks up the array's
+// device address with cudaGetSymbolAddress and caches it; that first call should be
+// made before any stream capture begins.  All calls share the one array and it keeps
+// the contents of the last call, so two calls whose work overlaps on the GPU (other
+// streams, other host threads) race on it; the check record is cleared on each call,
+// and every carried key is written before it is read.
+// ---------------------------------------------------------------------------------
+namespace knn {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[KNN_NOALLOC_SCRATCH_BYTES];
+
+constexpr size_t NOALLOC_HEADER = 256;   // check record of R
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// device address of the scratch array on the current device (looked up once per device)
+static knn_status noalloc_scratch(void** out) {
+    int dev = 0;
+    KNN_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(KNN_EUNSUPPORTED, "device ordinal %d too large", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(KNN_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return KNN_OK;
+}
+
+}  // namespace knn
+
+extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, int32_t k, const knn_join_opts* opts,
+                                       int32_t* out_ids, void* out_scores, void* stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!ix) return fail(KNN_EINVAL, "index is NULL");
+    if (!R) return fail(KNN_EINVAL, "R is NULL");
+    if (k < 1) return fail(KNN_EINVAL, "k must be >= 1");
+    if (k > KNN_MAX_K) return fail(KNN_EUNSUPPORTED, "k > %d", KNN_MAX_K);
+    if (R->dim != ix->dim) return fail(KNN_EINVAL, "R has dim %d, the index %d", R->dim, ix->dim);
+    if (R->dtype != ix->dtype) return fail(KNN_EINVAL, "R and the index have different dtypes");
+    if (!R->on_device) return fail(KNN_EINVAL, "knn_join_noalloc needs R in device memory (on_device = 1)");
+    knn_join_opts o = {};
+    if (opts) o = *opts;
+    if (o.mode != KNN_MODE_IIIB && o.mode != KNN_MODE_IIB) return fail(KNN_EINVAL, "unknown mode");
+    if (o.outputs_on_host) return fail(KNN_EINVAL, "knn_join_noalloc writes device outputs only");
+    if (R->n_rows > 0 && (!out_ids || !out_scores)) return fail(KNN_EINVAL, "outputs are NULL");
+    const size_t carry_cap = (KNN_NOALLOC_SCRATCH_BYTES - NOALLOC_HEADER) / sizeof(u64);
+    if ((uint64_t)R->n_rows * (uint64_t)k > carry_cap)
+        return fail(KNN_EUNSUPPORTED,
+                    "knn_join_noalloc: n_rows * k = %lld exceeds the %zu top-k keys its %d-byte scratch holds",
+                    (long long)R->n_rows * k, carry_cap, (int)KNN_NOALLOC_SCRATCH_BYTES);
+    void* scratch = nullptr;
+    KNN_TRY(noalloc_scratch(&scratch));
+
+    DevCSR r;
+    KNN_TRY(check_device_csr_into(R, scratch, !o.skip_validation, stream, &r));
+    if (r.n_rows == 0) return KNN_OK;
+    if (ix->dtype == KNN_U8) {
+        double bound = std::min(r.max_row_sum * ix->max_w, ix->max_row_sum * r.max_w);
+        if (bound >= 2147483647.0) return fail(KNN_EUNSUPPORTED, "uint8 scores could overflow int32");
+    }
+    const int nb = ix->block_size;
+    int T = o.threads ? o.threads : 512;
+    if (T < 128 || T > 1024 || (T & 31)) return fail(KNN_EINVAL, "threads must be a multiple of 32 in [128, 1024]");
+    while (nb / (T * 4) > 16) T *= 2;
+    while (T > 32 && nb < T * 4) T /= 2;
+    if (nb % (T * 4) || nb / (T * 4) > 16 || T > 1024)
+        return fail(KNN_EUNSUPPORTED, "block size %d does not fit %d threads", nb, T);
+    const int max_r = std::max(1, r.max_row_nnz);
+    SmemLayout L = smem_layout(nb, max_r);
+    int dev = 0, smem_optin = 0;
+    KNN_CUDA_TRY(cudaGetDevice(&dev));
+    KNN_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (L.total + sizeof(CtaState) + 32 * 8 * 2 + 64 > (size_t)smem_optin)
+        return fail(KNN_EUNSUPPORTED, "a row with %d features and S blocks of %d need %zu bytes of shared memory (> %d)",
+                    max_r, nb, L.total, smem_optin);
+    if (r.n_rows > (int64_t)INT32_MAX) return fail(KNN_EUNSUPPORTED, "too many rows");
+
+    JoinParams p;
+    memset(&p, 0, sizeof(p));
+    p.n_rows = r.n_rows;
+    p.r_indptr = r.indptr;
+    p.r_idx = r.indices;
+    p.r_val = r.values;
+    p.n_s = ix->n_rows;
+    p.dim = ix->dim;
+    p.n_blocks = ix->n_blocks;
+    p.n_levels = ix->n_levels;
+    p.block_shift = ix->block_shift;
+    p.binoff = ix->binoff;
+    p.postings = ix->postings;
+    p.s_indptr = ix->s_indptr;
+    p.sp_d = ix->sp_d;
+    p.sp_w = ix->sp_w;
+    p.n_unidx = ix->n_unidx;
+    p.ubound = ix->ubound;
+    memcpy(p.levels, ix->levels, sizeof(p.levels));
+    p.k = k;
+    p.groups = 1;   // one group per row: the only schedule whose scratch is the carry buffer
+    p.blocks_per_group = ix->n_blocks;
+    p.iiib = o.mode == KNN_MODE_IIIB && ix->n_levels > 1;
+    p.max_r_nnz = max_r;
+    p.init_thr = o.init_threshold;
+    p.out_ids = out_ids;
+    p.out_scores = out_scores;
+    p.n_found = o.n_found;
+    p.touched = (unsigned long long*)o.postings_scanned;
+    p.stats = (unsigned long long*)o.stats;
+    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 0.25f;
+    if (!(p.level_margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
+    p.carry = (u64*)((unsigned char*)scratch + NOALLOC_HEADER);
+
+    if (ix->dtype == KNN_U8)
+        KNN_CUDA_TRY(cudaFuncSetAttribute(k_join<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    else
+        KNN_CUDA_TRY(cudaFuncSetAttribute(k_join<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    const int per_launch = std::min(ix->n_blocks, o.blocks_per_launch > 0 ? o.blocks_per_launch : 8);
+    const int n_launch = (int)ceil_div(ix->n_blocks, per_launch);
+    for (int li = 0; li < n_launch; li++) {
+        p.block_begin = li * per_launch;
+        p.block_end = std::min(ix->n_blocks, (li + 1) * per_launch);
+        p.carry_in = li > 0;
+        p.carry_out = li + 1 < n_launch;
+        if (ix->dtype == KNN_U8)
+            k_join<uint8_t><<<(unsigned)r.n_rows, T, L.total, stream>>>(p);
+        else
+            k_join<float><<<(unsigned)r.n_rows, T, L.total, stream>>>(p);
+        KNN_CUDA_TRY(cudaGetLastError());
+        count_launch();
     }
     return KNN_OK;
 }

@@ -245,6 +245,74 @@ knn_status prepare_csr(const knn_csr* in, cudaStream_t stream, Buffers& bufs, bo
     return KNN_OK;
 }
 
+// Validation and row statistics of a CSR already on the device, with the check record
+// in caller-provided device memory (at least 256 bytes, any contents) instead of an
+// allocation.  Used by the allocation-free join; synchronises the stream.
+knn_status check_device_csr_into(const knn_csr* in, void* scratch, bool validate, cudaStream_t stream,
+                                 DevCSR* out) {
+    if (!in) return fail(KNN_EINVAL, "CSR pointer is NULL");
+    if (!in->on_device) return fail(KNN_EINVAL, "this call needs R in device memory (on_device = 1)");
+    if (in->n_rows < 0) return fail(KNN_EINVAL, "n_rows < 0");
+    if (in->dim < 1) return fail(KNN_EINVAL, "dim must be >= 1");
+    if (in->dtype != KNN_U8 && in->dtype != KNN_F32) return fail(KNN_EINVAL, "unknown dtype");
+    if (!in->indptr) return fail(KNN_EINVAL, "indptr is NULL");
+    static_assert(sizeof(CsrCheck) <= 256, "check record must fit the scratch header");
+    const int64_t n = in->n_rows;
+    int64_t ends[2];
+    KNN_CUDA_TRY(cudaMemcpyAsync(&ends[0], in->indptr, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+    KNN_CUDA_TRY(cudaMemcpyAsync(&ends[1], in->indptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+    KNN_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (ends[0] != 0) return fail(KNN_EINVAL, "indptr[0] must be 0");
+    const int64_t nnz = ends[1];
+    if (nnz < 0) return fail(KNN_EINVAL, "indptr[n_rows] < 0");
+    if (nnz > (int64_t)INT32_MAX) return fail(KNN_EUNSUPPORTED, "more than 2^31-1 features");
+    if (nnz > 0 && (!in->indices || !in->values)) return fail(KNN_EINVAL, "indices/values are NULL");
+    out->n_rows = n;
+    out->nnz = nnz;
+    out->dim = in->dim;
+    out->dtype = in->dtype;
+    out->indptr = in->indptr;
+    out->indices = in->indices;
+    out->values = in->values;
+    CsrCheck* chk = (CsrCheck*)scratch;
+    KNN_CUDA_TRY(cudaMemsetAsync(chk, 0, sizeof(CsrCheck), stream));   // the record starts at zero
+    CsrCheck h;
+    if (validate) {
+        k_check_indptr<<<launch_blocks(n + 1, 256), 256, 0, stream>>>(in->indptr, n, nnz, chk);
+        KNN_CUDA_TRY(cudaGetLastError());
+        count_launch();
+        KNN_CUDA_TRY(cudaMemcpyAsync(&h, chk, sizeof(h), cudaMemcpyDeviceToHost, stream));
+        KNN_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (h.flags & BAD_INDPTR) return fail(KNN_EINVAL, "indptr is not a non-decreasing sequence from 0 to nnz");
+    }
+    if (n > 0) {
+        int blocks = launch_blocks(n * 32, 256, 152 * 64);
+        if (in->dtype == KNN_U8)
+            k_check_rows<uint8_t><<<blocks, 256, 0, stream>>>(in->indptr, in->indices, (const uint8_t*)in->values,
+                                                             n, in->dim, chk);
+        else
+            k_check_rows<float><<<blocks, 256, 0, stream>>>(in->indptr, in->indices, (const float*)in->values, n,
+                                                           in->dim, chk);
+        KNN_CUDA_TRY(cudaGetLastError());
+        count_launch();
+    }
+    KNN_CUDA_TRY(cudaMemcpyAsync(&h, chk, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    KNN_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (validate) {
+        if (h.flags & BAD_DIM) return fail(KNN_EINVAL, "a feature dimension is outside [0, dim)");
+        if (h.flags & BAD_ORDER) return fail(KNN_EINVAL, "features of a row are not strictly ascending");
+        if (h.flags & BAD_WEIGHT) return fail(KNN_EINVAL, "a weight is not > 0 (or not finite)");
+    }
+    out->max_row_nnz = h.max_nnz;
+    float mw;
+    memcpy(&mw, &h.max_w_bits, 4);
+    out->max_w = mw;
+    double ms;
+    memcpy(&ms, &h.max_sum_bits, 8);
+    out->max_row_sum = ms;
+    return KNN_OK;
+}
+
 // ---------------------------------------------------------------------------------
 // exclusive scan of u32
 // ---------------------------------------------------------------------------------
