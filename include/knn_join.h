@@ -192,6 +192,89 @@ knn_status knn_join(const knn_index* index, const knn_csr* R, int32_t k,
                     void* stream);
 
 /* ------------------------------------------------------------------------------ */
+/* Learned start threshold (not in the paper: it generalises Section 4.4's           */
+/* MinPruneScore, a threshold derived from earlier work, to one predicted per query) */
+/* ------------------------------------------------------------------------------ */
+
+typedef struct knn_model knn_model;   /* opaque; owns its device parameters */
+
+typedef struct {
+    uint64_t seed;        /* initial weights and the sketch's hash seed */
+} knn_model_opts;
+
+typedef struct {
+    int32_t epochs;       /* 0 = 20 */
+    int32_t batch;        /* rows per step; 0 = 512 */
+    float lr;             /* Adam step size; 0 = 1e-3 */
+    float quantile;       /* pinball-loss quantile q in (0,1); 0 = 0.1.  Low q makes the
+                             prediction sit below the true k-th score more often.     */
+    uint64_t seed;        /* batch order */
+} knn_train_opts;
+
+/* Creates a model: sketch of 516 values per query (512 signed hash buckets of the
+ * features, normalised by ||r||_2, and log1p of nnz, weight sum, ||r||_2, max weight)
+ * -> 256 -> 256 -> 1 with ReLU, BF16 weights, FP32 accumulation.  It predicts
+ * log(k-th best score).                                                            */
+knn_status knn_threshold_model_create(const knn_model_opts* opts, void* stream, knn_model** out);
+void knn_threshold_model_destroy(knn_model* model);
+
+/* Trains on queries Q (host or device CSR) and their exact k-th best scores
+ * (device float[Q.n_rows], from knn_join; rows with no k-th score, value 0, are
+ * skipped) with the pinball loss at the given quantile and Adam, on the GPU.
+ * final_loss (host, may be NULL) receives the last epoch's mean loss.  Synchronises. */
+knn_status knn_threshold_model_train(knn_model* model, const knn_csr* Q, const float* kth_scores,
+                                     const knn_train_opts* opts, float* final_loss, void* stream);
+
+/* out_tau: device float[R.n_rows], the predicted k-th best score of each row. */
+knn_status knn_threshold_model_predict(const knn_model* model, const knn_csr* R, float* out_tau,
+                                       void* stream);
+
+/* Save / load: all parameters and optimiser state as one host buffer.  With
+ * host_buf = NULL, get_params only reports the size in *needed.                  */
+knn_status knn_threshold_model_get_params(const knn_model* model, void* host_buf, size_t bytes,
+                                          size_t* needed);
+knn_status knn_threshold_model_set_params(knn_model* model, const void* host_buf, size_t bytes);
+
+typedef struct {
+    knn_join_opts join;   /* options of both passes (init_threshold, n_found are set here) */
+    float tau_scale;      /* multiplies the predictions (0 = 1)                          */
+    const float* tau;     /* device float[n_rows]: start thresholds to use instead of the
+                             model's (the model may then be NULL)                       */
+} knn_learned_opts;
+
+typedef struct {
+    int64_t rows;           /* rows joined                                              */
+    int64_t fallback_rows;  /* rows rejoined with the plain threshold (found < k)       */
+} knn_learned_stats;
+
+/* Exact top-k like knn_join, starting each row from a predicted threshold: every s with
+ * score >= tau is kept; a row that ends with k entries is exact, the others are joined
+ * again with the plain threshold on the device.  Same outputs and errors as knn_join;
+ * stats (host, may be NULL).  Synchronises `stream`.                                */
+knn_status knn_join_learned(const knn_index* index, const knn_model* model, const knn_csr* R,
+                            int32_t k, const knn_learned_opts* opts, int32_t* out_ids,
+                            void* out_scores, knn_learned_stats* stats, void* stream);
+
+/* Test and inspection hooks of the model's kernels (no paper counterpart).
+ *   knn_gemm_bf16: C[m*scm + n*scn] (+)= sum_k A[m*sam + k*sak] * B[k*sbk + n*sbn] on
+ *     tensor cores (bf16 inputs, fp32 accumulation), all device pointers.
+ *   knn_threshold_sketch: device bf16 [R.n_rows][528] sketches (columns 516.. are 0).
+ *   knn_threshold_model_forward_backward: one forward and backward pass on device bf16
+ *     inputs x [B][528] and targets (log k-th scores) at a quantile; writes device
+ *     predictions [B] and gradients of the mean loss [n_params].
+ *   knn_threshold_model_params: device pointer to the fp32 parameters
+ *     (W1 [256][528], b1 [256], W2 [256][256], b2 [256], w3 [256], b3 [1]).       */
+knn_status knn_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int64_t sam, int64_t sak,
+                         const void* B, int64_t sbk, int64_t sbn, float* C, int64_t scm, int64_t scn,
+                         int32_t accumulate, void* stream);
+knn_status knn_threshold_sketch(const knn_model* model, const knn_csr* R, void* out_x_bf16,
+                                void* stream);
+knn_status knn_threshold_model_forward_backward(knn_model* model, const void* x_bf16,
+                                                const float* target, int64_t B, float quantile,
+                                                float* out_pred, float* out_grads, void* stream);
+knn_status knn_threshold_model_params(const knn_model* model, const float** params, int64_t* n);
+
+/* ------------------------------------------------------------------------------ */
 /* Allocation-free join.  The paper has no counterpart: this is an engineering      */
 /* variant of knn_join for callers that cannot let a library allocate device memory */
 /* during a call -- e.g. a server that has split the GPU between its own fixed      */

@@ -297,3 +297,188 @@ def knn_join_noalloc(index: Index, R: DeviceCSR, k: int, out_ids: torch.Tensor, 
     _check(L, L.knn_join_noalloc(index.handle, ctypes.byref(c), int(k), ctypes.byref(opts),
                                  out_ids.data_ptr(), out_scores.data_ptr(), _stream_ptr(stream)))
     return out_ids, out_scores
+
+
+# ----------------------------------------------------------------------------------
+# learned start threshold
+# ----------------------------------------------------------------------------------
+
+class _ModelOpts(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64)]
+
+
+class _TrainOpts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("quantile", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class _LearnedOpts(ctypes.Structure):
+    _fields_ = [("join", _JoinOpts), ("tau_scale", ctypes.c_float), ("tau", ctypes.c_void_p)]
+
+
+class _LearnedStats(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("fallback_rows", ctypes.c_int64)]
+
+
+SKETCH_WIDTH = 528   # padded sketch row (516 used)
+HIDDEN = 256
+
+
+def _model_lib():
+    L = lib()
+    if not getattr(L, "_model_ready", False):
+        P = ctypes.POINTER
+        L.knn_threshold_model_create.argtypes = [P(_ModelOpts), ctypes.c_void_p, P(ctypes.c_void_p)]
+        L.knn_threshold_model_destroy.argtypes = [ctypes.c_void_p]
+        L.knn_threshold_model_destroy.restype = None
+        L.knn_threshold_model_train.argtypes = [ctypes.c_void_p, P(_Csr), ctypes.c_void_p, P(_TrainOpts),
+                                                P(ctypes.c_float), ctypes.c_void_p]
+        L.knn_threshold_model_predict.argtypes = [ctypes.c_void_p, P(_Csr), ctypes.c_void_p, ctypes.c_void_p]
+        L.knn_threshold_model_get_params.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                                     P(ctypes.c_size_t)]
+        L.knn_threshold_model_set_params.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+        L.knn_join_learned.argtypes = [ctypes.c_void_p, ctypes.c_void_p, P(_Csr), ctypes.c_int32,
+                                       P(_LearnedOpts), ctypes.c_void_p, ctypes.c_void_p, P(_LearnedStats),
+                                       ctypes.c_void_p]
+        L.knn_gemm_bf16.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                    ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int32, ctypes.c_void_p]
+        L.knn_threshold_sketch.argtypes = [ctypes.c_void_p, P(_Csr), ctypes.c_void_p, ctypes.c_void_p]
+        L.knn_threshold_model_forward_backward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                           ctypes.c_int64, ctypes.c_float, ctypes.c_void_p,
+                                                           ctypes.c_void_p, ctypes.c_void_p]
+        L.knn_threshold_model_params.argtypes = [ctypes.c_void_p, P(ctypes.c_void_p), P(ctypes.c_int64)]
+        L._model_ready = True
+    return L
+
+
+class ThresholdModel:
+    """knn_model handle: sketch -> 516-256-256-1 MLP (BF16 weights) predicting log k-th score."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        L = _model_lib()
+        h = ctypes.c_void_p()
+        _check(L, L.knn_threshold_model_create(ctypes.byref(_ModelOpts(int(seed))), _stream_ptr(stream),
+                                               ctypes.byref(h)))
+        self._h = h.value
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("model is closed")
+        return self._h
+
+    def train(self, Q, kth_scores: torch.Tensor, epochs: int = 0, batch: int = 0, lr: float = 0.0,
+              quantile: float = 0.0, seed: int = 0, stream=None) -> float:
+        L = _model_lib()
+        keep = []
+        c = _csr(Q, keep)
+        loss = ctypes.c_float(0.0)
+        o = _TrainOpts(int(epochs), int(batch), float(lr), float(quantile), int(seed))
+        kth = kth_scores.contiguous().float()
+        _check(L, L.knn_threshold_model_train(self.handle, ctypes.byref(c), kth.data_ptr(), ctypes.byref(o),
+                                              ctypes.byref(loss), _stream_ptr(stream)))
+        return float(loss.value)
+
+    def predict(self, R, stream=None) -> torch.Tensor:
+        L = _model_lib()
+        keep = []
+        c = _csr(R, keep)
+        out = torch.empty(c.n_rows, dtype=torch.float32, device="cuda")
+        _check(L, L.knn_threshold_model_predict(self.handle, ctypes.byref(c), out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def sketch(self, R, stream=None) -> torch.Tensor:
+        L = _model_lib()
+        keep = []
+        c = _csr(R, keep)
+        out = torch.empty((c.n_rows, SKETCH_WIDTH), dtype=torch.bfloat16, device="cuda")
+        _check(L, L.knn_threshold_sketch(self.handle, ctypes.byref(c), out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def params(self) -> torch.Tensor:
+        """fp32 parameters (a copy): W1 [256,528], b1, W2 [256,256], b2, w3 [256], b3 [1]."""
+        L = _model_lib()
+        p = ctypes.c_void_p()
+        n = ctypes.c_int64()
+        _check(L, L.knn_threshold_model_params(self.handle, ctypes.byref(p), ctypes.byref(n)))
+        torch.cuda.synchronize()
+
+        class _Dev:   # a view of the library's device array for torch.as_tensor
+            __cuda_array_interface__ = {"shape": (n.value,), "typestr": "<f4", "data": (p.value, False),
+                                        "version": 3}
+        return torch.as_tensor(_Dev(), device="cuda").clone()
+
+    def forward_backward(self, x_bf16: torch.Tensor, target: torch.Tensor, quantile: float, stream=None):
+        L = _model_lib()
+        B = x_bf16.shape[0]
+        pred = torch.empty(B, dtype=torch.float32, device="cuda")
+        n = ctypes.c_int64()
+        p = ctypes.c_void_p()
+        _check(L, L.knn_threshold_model_params(self.handle, ctypes.byref(p), ctypes.byref(n)))
+        grads = torch.empty(n.value, dtype=torch.float32, device="cuda")
+        _check(L, L.knn_threshold_model_forward_backward(self.handle, x_bf16.contiguous().data_ptr(),
+                                                         target.contiguous().float().data_ptr(), B,
+                                                         float(quantile), pred.data_ptr(), grads.data_ptr(),
+                                                         _stream_ptr(stream)))
+        return pred, grads
+
+    def get_params(self) -> bytes:
+        L = _model_lib()
+        need = ctypes.c_size_t()
+        _check(L, L.knn_threshold_model_get_params(self.handle, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        _check(L, L.knn_threshold_model_get_params(self.handle, buf, need.value, ctypes.byref(need)))
+        return buf.raw
+
+    def set_params(self, data: bytes):
+        L = _model_lib()
+        buf = ctypes.create_string_buffer(data, len(data))
+        _check(L, L.knn_threshold_model_set_params(self.handle, buf, len(data)))
+
+    def close(self):
+        if self._h:
+            _model_lib().knn_threshold_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def knn_gemm_bf16(A: torch.Tensor, sa, B: torch.Tensor, sb, C: torch.Tensor, sc, M, N, K, accumulate=False,
+                  stream=None):
+    """C (+)= A @ B on tensor cores with explicit element strides (test hook)."""
+    L = _model_lib()
+    _check(L, L.knn_gemm_bf16(M, N, K, A.data_ptr(), sa[0], sa[1], B.data_ptr(), sb[0], sb[1], C.data_ptr(),
+                              sc[0], sc[1], int(accumulate), _stream_ptr(stream)))
+
+
+def knn_join_learned(index: Index, model: "ThresholdModel | None", R, k: int, *, tau: torch.Tensor | None = None,
+                     tau_scale: float = 0.0, mode: str = "iiib", threads: int = 0, s_groups: int = 0,
+                     postings_scanned: torch.Tensor | None = None, stats_out: torch.Tensor | None = None,
+                     level_margin: float = 0.0, blocks_per_launch: int = 0, out_ids=None, out_scores=None,
+                     stream=None):
+    """Exact top-k from predicted start thresholds with verify-and-fallback.
+
+    Returns (ids, scores, {"rows": n, "fallback_rows": m}).
+    """
+    L = _model_lib()
+    keep = []
+    c = _csr(R, keep)
+    n = c.n_rows
+    sdt = torch.int32 if index.dtype == KNN_U8 else torch.float32
+    if out_ids is None:
+        out_ids = torch.empty((n, k), dtype=torch.int32, device="cuda")
+        out_scores = torch.empty((n, k), dtype=sdt, device="cuda")
+    jo = _JoinOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), int(s_groups), None, None,
+                   _ptr(postings_scanned), 0, 0, float(level_margin), _ptr(stats_out), int(blocks_per_launch))
+    lo = _LearnedOpts(jo, float(tau_scale), _ptr(tau))
+    st = _LearnedStats()
+    _check(L, L.knn_join_learned(index.handle, model.handle if model is not None else None, ctypes.byref(c),
+                                 int(k), ctypes.byref(lo), out_ids.data_ptr(), out_scores.data_ptr(),
+                                 ctypes.byref(st), _stream_ptr(stream)))
+    return out_ids, out_scores, {"rows": int(st.rows), "fallback_rows": int(st.fallback_rows)}

@@ -140,6 +140,10 @@ inline int launch_blocks(int64_t work, int per_block, int64_t cap = (1LL << 31) 
     return (int)b;
 }
 
+// Predicted k-th scores (device float[n_rows]) of a device CSR with the model.
+knn_status model_predict_tau(const knn_model* md, const DevCSR& r, float tau_scale, float* tau, cudaStream_t s,
+                             Buffers& tmp);
+
 // Exclusive scan of u32 counts (n elements) into out[0..n], out[n] = total.
 // The total must stay below 2^32 (checked by the caller).  Works in place.
 knn_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t stream,

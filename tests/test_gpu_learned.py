@@ -1,0 +1,252 @@
+"""The learned start threshold: tensor-core GEMM, sketch, MLP forward/backward against
+fp64 references, training, and the learned join's exactness (verify-and-fallback)."""
+import numpy as np
+import pytest
+
+from paper_1011_2807_gb300 import synth
+import compare
+
+pytestmark = pytest.mark.gpu
+
+W1_SHAPE = (256, 528)
+OFF_B1 = 256 * 528
+OFF_W2 = OFF_B1 + 256
+OFF_B2 = OFF_W2 + 256 * 256
+OFF_W3 = OFF_B2 + 256
+OFF_B3 = OFF_W3 + 256
+
+
+@pytest.fixture(scope="module")
+def knn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1011_2807_gb300 as knn
+    knn.lib()
+    return knn
+
+
+def bf16_round(a):
+    import torch
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+# ----------------------------------------------------------------------------------
+# GEMM on tensor cores
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M,N,K", [(64, 64, 32), (100, 70, 53), (3, 300, 528), (256, 256, 1000), (1, 1, 1)])
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True)])
+def test_gemm_bf16(knn, M, N, K, ta, tb):
+    import torch
+    from paper_1011_2807_gb300.binding import knn_gemm_bf16
+    g = torch.Generator().manual_seed(M * 7 + N + K)
+    A = torch.randn((K, M) if ta else (M, K), generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn((N, K) if tb else (K, N), generator=g).to(torch.bfloat16).cuda()
+    sa = (1, M) if ta else (K, 1)
+    sb = (1, K) if tb else (N, 1)
+    C = torch.full((M, N), 3.0, device="cuda")
+    knn_gemm_bf16(A, sa, B, sb, C, (N, 1), M, N, K)
+    torch.cuda.synchronize()
+    Ad = A.double().cpu().numpy()
+    Bd = B.double().cpu().numpy()
+    ref = (Ad.T if ta else Ad) @ (Bd.T if tb else Bd)
+    np.testing.assert_allclose(C.cpu().numpy(), ref, rtol=1e-4, atol=1e-4 * np.sqrt(K))
+    knn_gemm_bf16(A, sa, B, sb, C, (N, 1), M, N, K, accumulate=True)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(C.cpu().numpy(), 2 * ref, rtol=1e-4, atol=2e-4 * np.sqrt(K))
+
+
+# ----------------------------------------------------------------------------------
+# sketch
+# ----------------------------------------------------------------------------------
+
+def mix32(x):
+    x = x.astype(np.uint64) & 0xFFFFFFFF
+    x ^= x >> 16
+    x = (x * 0x85EBCA6B) & 0xFFFFFFFF
+    x ^= x >> 13
+    x = (x * 0xC2B2AE35) & 0xFFFFFFFF
+    x ^= x >> 16
+    return x
+
+
+def sketch_ref(R, model_seed):
+    seed = (model_seed ^ 0x5BD1E995) & 0xFFFFFFFF
+    out = np.zeros((R.n_rows, 528))
+    for i in range(R.n_rows):
+        d, w = R.row(i)
+        w = w.astype(np.float64)
+        norm = np.sqrt((w * w).sum())
+        h = mix32((d.astype(np.uint64) * 0x9E3779B1 + seed) & 0xFFFFFFFF)
+        sign = np.where(h >> 31, -1.0, 1.0)
+        np.add.at(out[i], (h & 511).astype(np.int64), sign * w / norm)
+        out[i, 512:516] = np.log1p([len(d), w.sum(), norm, w.max()])
+    return out
+
+
+def test_sketch(knn):
+    R = synth.spectrum_u8(64, 301, role="R")
+    m = knn.ThresholdModel(seed=17)
+    X = m.sketch(knn.DeviceCSR.from_host(R)).float().cpu().numpy()
+    ref = sketch_ref(R, 17)
+    np.testing.assert_allclose(X, bf16_round(ref), rtol=1e-2, atol=2e-3)
+    assert (X[:, 516:] == 0).all()
+    m.close()
+
+
+# ----------------------------------------------------------------------------------
+# forward / backward against an fp64 restatement (itself pinned by finite differences)
+# ----------------------------------------------------------------------------------
+
+def mlp_ref(p, x, t, q, round_like_gpu=True):
+    """fp64 forward and gradients of the mean pinball loss at quantile q."""
+    rb = bf16_round if round_like_gpu else (lambda a: np.asarray(a, np.float64))
+    W1 = rb(p[:OFF_B1].reshape(W1_SHAPE))
+    b1 = p[OFF_B1:OFF_W2].astype(np.float64)
+    W2 = rb(p[OFF_W2:OFF_B2].reshape(256, 256))
+    b2 = p[OFF_B2:OFF_W3].astype(np.float64)
+    w3 = rb(p[OFF_W3:OFF_B3])
+    b3 = float(p[OFF_B3])
+    B = x.shape[0]
+    H1 = rb(np.maximum(x @ W1.T + b1, 0.0))
+    H2 = rb(np.maximum(H1 @ W2.T + b2, 0.0))
+    y = H2 @ w3 + b3
+    e = t - y
+    loss = np.where(e > 0, q * e, (q - 1) * e).mean()
+    g = np.where(e > 0, -q, 1 - q) / B
+    dw3 = g @ H2
+    db3 = g.sum()
+    dH2 = rb(np.outer(g, w3) * (H2 > 0))
+    db2 = dH2.sum(0)
+    dW2 = dH2.T @ H1
+    dH1 = rb((dH2 @ W2) * (H1 > 0))
+    db1 = dH1.sum(0)
+    dW1 = dH1.T @ x
+    grads = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dw3, [db3]])
+    return y, grads, loss
+
+
+def test_reference_backward_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    p = rng.normal(0, 0.05, size=OFF_B3 + 1)
+    x = rng.normal(0, 1, size=(6, 528))
+    x[:, 516:] = 0
+    t = rng.normal(0, 1, size=6)
+    _, g, _ = mlp_ref(p, x, t, 0.3, round_like_gpu=False)
+    for idx in [5, 528 * 3 + 7, OFF_B1 + 9, OFF_W2 + 1000, OFF_B2 + 3, OFF_W3 + 11, OFF_B3]:
+        h = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[idx] += h
+        pm[idx] -= h
+        fd = (mlp_ref(pp, x, t, 0.3, False)[2] - mlp_ref(pm, x, t, 0.3, False)[2]) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 + 1e-4 * abs(g[idx]), (idx, fd, g[idx])
+
+
+@pytest.mark.parametrize("q", [0.1, 0.5])
+def test_forward_backward_vs_fp64(knn, q):
+    import torch
+    m = knn.ThresholdModel(seed=5)
+    R = synth.spectrum_u8(96, 311, role="R")
+    x = m.sketch(knn.DeviceCSR.from_host(R))
+    rng = np.random.default_rng(1)
+    t = torch.from_numpy(rng.normal(10.0, 0.5, size=R.n_rows).astype(np.float32)).cuda()
+    pred, grads = m.forward_backward(x, t, q)
+    torch.cuda.synchronize()
+    p = m.params().cpu().numpy()
+    y_ref, g_ref, _ = mlp_ref(p, x.float().cpu().numpy().astype(np.float64), t.cpu().numpy().astype(np.float64), q)
+    np.testing.assert_allclose(pred.cpu().numpy(), y_ref, rtol=1e-3, atol=1e-3)
+    g = grads.cpu().numpy()
+    for a, b in [(0, OFF_B1), (OFF_B1, OFF_W2), (OFF_W2, OFF_B2), (OFF_B2, OFF_W3), (OFF_W3, OFF_B3), (OFF_B3, OFF_B3 + 1)]:
+        err = np.linalg.norm(g[a:b] - g_ref[a:b])
+        assert err <= 2e-2 * np.linalg.norm(g_ref[a:b]) + 1e-7, (a, b, err, np.linalg.norm(g_ref[a:b]))
+    m.close()
+
+
+# ----------------------------------------------------------------------------------
+# training and the learned join
+# ----------------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def trained(knn):
+    import torch
+    S = synth.spectrum_u8(30000, 321, role="S")
+    T = synth.spectrum_u8(6000, 322, role="R")
+    idx = knn.knn_join_build_index(S, block_size=4096)
+    _, sc = knn.knn_join(idx, knn.DeviceCSR.from_host(T), 5)
+    kth = sc[:, 4].float()
+    m = knn.ThresholdModel(seed=3)
+    loss0 = m.train(T, kth, epochs=1, batch=256, quantile=0.1, seed=1)
+    loss1 = m.train(T, kth, epochs=25, batch=256, quantile=0.1, seed=2)
+    torch.cuda.synchronize()
+    yield dict(S=S, T=T, idx=idx, kth=kth, model=m, loss0=loss0, loss1=loss1)
+    m.close()
+    idx.close()
+
+
+def test_training_reduces_loss(trained):
+    assert trained["loss1"] < 0.7 * trained["loss0"], (trained["loss0"], trained["loss1"])
+
+
+def test_prediction_quantile(knn, trained):
+    tau = trained["model"].predict(trained["T"]).cpu().numpy()
+    kth = trained["kth"].cpu().numpy()
+    below = (tau <= kth).mean()
+    assert below > 0.6, below     # trained at q = 0.1: mostly below the true k-th score
+
+
+def test_save_load_roundtrip(knn, trained):
+    blob = trained["model"].get_params()
+    m2 = knn.ThresholdModel(seed=99)
+    m2.set_params(blob)
+    R = synth.spectrum_u8(50, 331, role="R")
+    a = trained["model"].predict(R).cpu().numpy()
+    b = m2.predict(R).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    m2.close()
+
+
+def test_learned_join_is_exact(knn, trained, oracle_mod):
+    import torch
+    E = synth.spectrum_u8(400, 341, role="R")
+    idx = trained["idx"]
+    Ed = knn.DeviceCSR.from_host(E)
+    pids, psc = knn.knn_join(idx, Ed, 5)
+    lids, lsc, st = knn.knn_join_learned(idx, trained["model"], Ed, 5)
+    torch.cuda.synchronize()
+    assert torch.equal(pids, lids) and torch.equal(psc, lsc)
+    assert st["rows"] == E.n_rows and 0 <= st["fallback_rows"] < E.n_rows
+    eids, esc, _ = oracle_mod.iib_join(E, trained["S"], 5, threads=8)
+    compare.assert_exact(lids.cpu().numpy(), lsc.cpu().numpy(), eids, esc, "learned")
+
+
+def test_over_predicting_thresholds_fall_back_everywhere(knn, trained):
+    import torch
+    E = synth.spectrum_u8(200, 351, role="R")
+    Ed = knn.DeviceCSR.from_host(E)
+    idx = trained["idx"]
+    pids, psc = knn.knn_join(idx, Ed, 5)
+    inf = torch.full((E.n_rows,), float("inf"), device="cuda")
+    lids, lsc, st = knn.knn_join_learned(idx, None, Ed, 5, tau=inf)
+    assert st["fallback_rows"] == E.n_rows
+    assert torch.equal(pids, lids) and torch.equal(psc, lsc)
+    zero = torch.zeros(E.n_rows, device="cuda")
+    lids, lsc, st = knn.knn_join_learned(idx, None, Ed, 5, tau=zero)
+    assert st["fallback_rows"] == 0
+    assert torch.equal(pids, lids) and torch.equal(psc, lsc)
+
+
+def test_good_thresholds_scan_fewer_postings(knn, trained):
+    import torch
+    E = synth.spectrum_u8(300, 361, role="R")
+    Ed = knn.DeviceCSR.from_host(E)
+    idx = trained["idx"]
+    c_plain = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pids, psc = knn.knn_join(idx, Ed, 5, s_groups=1, postings_scanned=c_plain)
+    tau = (psc[:, 4].float() * 0.9).contiguous()
+    c_l = torch.zeros(1, dtype=torch.int64, device="cuda")
+    lids, lsc, st = knn.knn_join_learned(idx, None, Ed, 5, tau=tau, s_groups=1, postings_scanned=c_l)
+    torch.cuda.synchronize()
+    assert st["fallback_rows"] == 0
+    assert torch.equal(pids, lids) and torch.equal(psc, lsc)
+    assert int(c_l.item()) < int(c_plain.item())
