@@ -37,6 +37,7 @@ typedef unsigned long long u64;
 constexpr int KMAX = KNN_MAX_K;
 constexpr int SORT_CAP = 1024;            // keys in the merge buffer (pushed + current top-k)
 constexpr int PUSH_CAP = SORT_CAP - KMAX;  // pushed candidates between merges
+constexpr int CQ_CAP = 256;                // entries queued for completion per pass
 
 __device__ __forceinline__ u64 make_key(uint32_t score_bits, uint32_t gid) {
     return ((u64)score_bits << 32) | (u64)(0xFFFFFFFFu - gid);
@@ -129,6 +130,7 @@ struct JoinParams {
     float levels[KNN_MAX_LEVELS];
     int32_t k, groups, blocks_per_group, iiib, max_r_nnz;
     float level_margin;
+    int32_t rden_dim;   // >0: r's uint8 weights are kept densely (rden_dim bytes, a multiple of 16)
     const float* init_thr;
     u64* part_keys;
     int32_t* out_ids;
@@ -144,12 +146,12 @@ struct JoinParams {
 };
 
 struct SmemLayout {
-    size_t acc, rf_d, rf_w, lbeg, lend, ipre, topk, sort, total;
+    size_t acc, rf_d, rf_w, lbeg, lend, ipre, topk, sort, cq, rden, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline SmemLayout smem_layout(int nb, int max_r_nnz) {
+__host__ __device__ inline SmemLayout smem_layout(int nb, int max_r_nnz, int rden_bytes = 0) {
     SmemLayout L;
     size_t o = 0;
     L.acc = o;  o = align16(o + (size_t)nb * 4);
@@ -160,6 +162,8 @@ __host__ __device__ inline SmemLayout smem_layout(int nb, int max_r_nnz) {
     L.ipre = o; o = align16(o + (size_t)(max_r_nnz + 1) * 4);
     L.topk = o; o = align16(o + (size_t)KMAX * 8);
     L.sort = o; o = align16(o + (size_t)SORT_CAP * 8);
+    L.cq = o;   o = align16(o + (size_t)CQ_CAP * 8);
+    L.rden = o; o = align16(o + (size_t)rden_bytes);
     L.total = o;
     return L;
 }
@@ -198,6 +202,7 @@ struct CtaState {
     double lbnd[KNN_MAX_LEVELS];  // residual bound of every level for this row
     unsigned long long n_steps, n_merges, n_rounds;  // work counters (thread 0)
     int next_list;  // next list of r to hand to a warp in the scan
+    int qcnt;       // entries in the completion queue
     int pred_level; // level the next block's list ranges were prefetched for (-1: none)
     // radix select of a candidate threshold (blocks with too many candidates)
     int rs_shift, rs_need, rs_done;
@@ -320,7 +325,7 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     __shared__ unsigned long long red_u[32];
 
     const int nb = 1 << p.block_shift;
-    const SmemLayout L = smem_layout(nb, p.max_r_nnz);
+    const SmemLayout L = smem_layout(nb, p.max_r_nnz, p.rden_dim);
     Acc* acc = (Acc*)(smem + L.acc);
     const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
     int32_t* rf_d = (int32_t*)(smem + L.rf_d);
@@ -328,6 +333,9 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     uint32_t* lbeg_buf = (uint32_t*)(smem + L.lbeg);
     uint32_t* lend_buf = (uint32_t*)(smem + L.lend);
     uint32_t* ipre = (uint32_t*)(smem + L.ipre);
+    uint32_t* cq_gid = (uint32_t*)(smem + L.cq);
+    Acc* cq_v = (Acc*)(smem + L.cq + CQ_CAP * 4);
+    uint8_t* rden = p.rden_dim ? (uint8_t*)(smem + L.rden) : nullptr;   // r's weights by dimension (uint8)
     u64* topk = (u64*)(smem + L.topk);
     u64* sortbuf = (u64*)(smem + L.sort);
 
@@ -350,8 +358,13 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     }
     for (int o = 16; o > 0; o >>= 1) mloc = fmax(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
     if (lane == 0) red_d[warp] = mloc;
-    // clear the accumulator
+    // clear the accumulator (and the dense copy of r)
     for (int i = tid * 4; i < nb; i += T * 4) *(int4*)(acc + i) = make_int4(0, 0, 0, 0);
+    if (rden) {
+        for (int i = tid * 16; i < p.rden_dim; i += T * 16) *(int4*)(rden + i) = make_int4(0, 0, 0, 0);
+        __syncthreads();
+        for (int i = tid; i < rn; i += T) rden[rf_d[i]] = (uint8_t)rf_w[i];
+    }
     __syncthreads();
     if (tid == 0) {
         double m = 0.0;
@@ -362,6 +375,7 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
         st.kth = 0ull;
         st.floor = p.init_thr ? JT<W>::floor_key(p.init_thr[row]) : ((u64)1 << 32);
         st.n_steps = st.n_merges = st.n_rounds = 0;
+        st.qcnt = 0;
         st.pred_level = -1;
         for (int l = 0; l < p.n_levels; l++) st.lbnd[l] = l ? JT<W>::level_bound(m, p.levels[l]) : 0.0;
     }
@@ -629,49 +643,72 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
         const bool one_round = st.pending <= PUSH_CAP;
         const int per_round = one_round ? 64 : max(1, PUSH_CAP / T);
         while (true) {
-            int done_here = 0;
             const u64 kth = st.kth;
             const u64 fl = st.floor;
             const double th = one_round ? st.theta
                                         : fmax(st.theta, JT<W>::score_of_bits((uint32_t)((kth > fl ? kth : fl) >> 32)));
             const Acc cm = one_round ? cmin : JT<W>::cheap_min(th, lb);
-            while (mask && done_here < per_round) {
-                int bit = __ffsll(mask) - 1;
-                mask &= mask - 1;
-                done_here++;
-                int c = bit >> 2, e = bit & 3;
-                int lid = c * T * 4 + tid * 4 + e;
-                Acc v = acc[lid];
-                acc[lid] = (Acc)0;
-                int64_t gid = gbase + lid;
-                if (v < cm) continue;   // the threshold rose in an earlier round
-                Acc full = v;
-                if (level > 0) {
-                    if (!JT<W>::exact_ok(v, M, p.ubound[(int64_t)level * p.n_s + gid], th)) continue;
-                    n_comp++;
-                    const int64_t j0 = p.s_indptr[gid];
-                    const int m = p.n_unidx[(int64_t)level * p.n_s + gid];
-                    n_resf += m;
-                    Acc res = (Acc)0;
-                    for (int q = 0; q < m; q++) {
-                        int32_t d = p.sp_d[j0 + q];
-                        Acc w = (Acc)((const W*)p.sp_w)[j0 + q];
-                        res += lookup_r<W>(rf_d, rf_w, rn, d) * w;
+            // (a) each thread takes its marked entries: level 0 pushes directly; above
+            //     level 0, entries within the per-vector bound go to the completion queue
+            int budget = per_round;
+            while (mask && budget > 0) {
+                const int bit = __ffsll(mask) - 1;
+                const int lid = (bit >> 2) * T * 4 + tid * 4 + (bit & 3);
+                const Acc v = acc[lid];
+                const int64_t gid = gbase + lid;
+                if (v >= cm) {
+                    if (level == 0) {
+                        u64 key = make_key(JT<W>::score_bits(v), (uint32_t)gid);
+                        if (key >= fl && key > kth) {
+                            sortbuf[atomicAdd(&st.cnt, 1)] = key;
+                            n_push++;
+                        }
+                    } else if (JT<W>::exact_ok(v, M, p.ubound[(int64_t)level * p.n_s + gid], th)) {
+                        const int slot = atomicAdd(&st.qcnt, 1);
+                        if (slot >= CQ_CAP) break;   // queue full: keep this entry for the next pass
+                        cq_gid[slot] = (uint32_t)gid;
+                        cq_v[slot] = v;
                     }
-                    full = v + res;
                 }
-                u64 key = make_key(JT<W>::score_bits(full), (uint32_t)gid);
-                if (key >= fl && key > kth) {
-                    int slot = atomicAdd(&st.cnt, 1);
-                    sortbuf[slot] = key;
-                    n_push++;
+                acc[lid] = (Acc)0;
+                mask &= mask - 1;
+                budget--;
+            }
+            __syncthreads();
+            // (b) completion of the queued entries (Algorithm 4's dot over the unindexed
+            //     features), one warp per entry, lanes over the features
+            const int nq = min(st.qcnt, CQ_CAP);
+            for (int e = warp; e < nq; e += nwarps) {
+                const int64_t gid = cq_gid[e];
+                const int64_t j0 = p.s_indptr[gid];
+                const int m = p.n_unidx[(int64_t)level * p.n_s + gid];
+                Acc res = (Acc)0;
+                for (int q = lane; q < m; q += 32) {
+                    const int32_t d = p.sp_d[j0 + q];
+                    const Acc w = (Acc)((const W*)p.sp_w)[j0 + q];
+                    const Acc rv = rden ? (Acc)rden[d] : lookup_r<W>(rf_d, rf_w, rn, d);
+                    res += rv * w;
+                }
+                for (int o = 16; o > 0; o >>= 1) res += __shfl_xor_sync(0xffffffffu, res, o);
+                if (lane == 0) {
+                    n_comp++;
+                    n_resf += m;
+                    const Acc full = cq_v[e] + res;
+                    u64 key = make_key(JT<W>::score_bits(full), (uint32_t)gid);
+                    if (key >= fl && key > kth) {
+                        sortbuf[atomicAdd(&st.cnt, 1)] = key;
+                        n_push++;
+                    }
                 }
             }
+            __syncthreads();
+            if (tid == 0) st.qcnt = 0;
+            const bool more = __syncthreads_or(mask != 0ull);
+            if (one_round && more) continue;   // only the completion queue filled up
             if (tid == 0 && st.cnt > 0) st.n_merges++;
             merge_topk(topk, sortbuf, st, p.k);
-            if (one_round) break;
+            if (!more) break;
             if (tid == 0) st.n_rounds++;
-            if (!__syncthreads_or(mask != 0ull)) break;
         }
         // publish this group's k-th key as a floor for the other groups of the row
         if (tid == 0 && p.floor_keys && st.size == p.k) atomicMax(p.floor_keys + row, st.kth);
@@ -767,7 +804,14 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     if (nb % (T * 4) || nb / (T * 4) > 16 || T > 1024)
         return fail(KNN_EUNSUPPORTED, "block size %d does not fit %d threads", nb, T);
     const int max_r = std::max(1, r.max_row_nnz);
-    SmemLayout L = smem_layout(nb, max_r);
+    // r's weights kept densely for completions (uint8, dimension up to 32768) when it
+    // still leaves room for two CTAs per SM
+    int rden_dim = 0;
+    if (ix->dtype == KNN_U8 && ix->dim <= 32768) {
+        const int rd = (int)((ix->dim + 15) & ~15);
+        if (smem_layout(nb, max_r, rd).total <= 110 * 1024) rden_dim = rd;
+    }
+    SmemLayout L = smem_layout(nb, max_r, rden_dim);
     int dev = 0;
     KNN_CUDA_TRY(cudaGetDevice(&dev));
     int smem_optin = 0, n_sm = 0;
@@ -821,6 +865,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     p.blocks_per_group = bpg;
     p.iiib = o.mode == KNN_MODE_IIIB && ix->n_levels > 1;
     p.max_r_nnz = max_r;
+    p.rden_dim = rden_dim;
     p.init_thr = o.init_threshold;
     p.out_ids = d_ids;
     p.out_scores = d_sc;
@@ -959,7 +1004,14 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     if (nb % (T * 4) || nb / (T * 4) > 16 || T > 1024)
         return fail(KNN_EUNSUPPORTED, "block size %d does not fit %d threads", nb, T);
     const int max_r = std::max(1, r.max_row_nnz);
-    SmemLayout L = smem_layout(nb, max_r);
+    // r's weights kept densely for completions (uint8, dimension up to 32768) when it
+    // still leaves room for two CTAs per SM
+    int rden_dim = 0;
+    if (ix->dtype == KNN_U8 && ix->dim <= 32768) {
+        const int rd = (int)((ix->dim + 15) & ~15);
+        if (smem_layout(nb, max_r, rd).total <= 110 * 1024) rden_dim = rd;
+    }
+    SmemLayout L = smem_layout(nb, max_r, rden_dim);
     int dev = 0, smem_optin = 0;
     KNN_CUDA_TRY(cudaGetDevice(&dev));
     KNN_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -992,6 +1044,7 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     p.blocks_per_group = ix->n_blocks;
     p.iiib = o.mode == KNN_MODE_IIIB && ix->n_levels > 1;
     p.max_r_nnz = max_r;
+    p.rden_dim = rden_dim;
     p.init_thr = o.init_threshold;
     p.out_ids = out_ids;
     p.out_scores = out_scores;
