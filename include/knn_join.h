@@ -192,6 +192,57 @@ knn_status knn_join(const knn_index* index, const knn_csr* R, int32_t k,
                     void* stream);
 
 /* ------------------------------------------------------------------------------ */
+/* Batched joins (no paper counterpart: many independent joins of Section 3 in one   */
+/* persistent launch, replayed as a CUDA graph)                                     */
+/* ------------------------------------------------------------------------------ */
+
+typedef struct {
+    const knn_index* index;   /* this join's S                                        */
+    knn_csr R;                /* its queries, in device memory (on_device = 1)        */
+    int32_t k;                /* 1..KNN_MAX_K                                         */
+    int32_t* out_ids;         /* device int32 [R.n_rows * k]                          */
+    void* out_scores;         /* device int32 / float [R.n_rows * k]                  */
+} knn_job;
+
+typedef struct {
+    knn_mode mode;
+    int32_t threads;            /* threads per CTA for every job, power of two; 0 = 512.
+                                   Every job's S block must lie in [4*threads, 64*threads]. */
+    int32_t blocks_per_group;   /* S blocks per work item; 0 = 8                             */
+    float level_margin;         /* as in knn_join_opts (0 = 0.25)                            */
+    int32_t use_graph;          /* knn_batch_create: capture the launch into a CUDA graph   */
+    int32_t skip_validation;    /* 1: trust every R                                          */
+    int64_t* stats;             /* device int64[KNN_STATS_LEN] or NULL (all jobs together)   */
+} knn_batch_opts;
+
+typedef struct knn_batch knn_batch;   /* a prepared batch (validated jobs, work items, scratch) */
+
+typedef struct {
+    int64_t work_items;       /* (job, S-block group, row) items of one run              */
+    int32_t ctas, threads;    /* persistent grid                                          */
+    int64_t shared_bytes;     /* dynamic shared memory per CTA                            */
+    int32_t graph;            /* 1 if runs replay a captured CUDA graph                  */
+    int32_t kernels_per_launch;
+} knn_batch_info;
+
+/* Prepares n_jobs joins: validates each R (synchronises `stream`), splits each job's S
+ * blocks into groups of blocks_per_group, orders the work items (largest first) and,
+ * with use_graph, captures the launch sequence into a CUDA graph.  The jobs' arrays
+ * must stay valid and unchanged in size while the batch exists (contents may change
+ * between launches).                                                                 */
+knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, const knn_batch_opts* opts,
+                            void* stream, knn_batch** out);
+/* Runs every job (asynchronously on `stream`): one persistent kernel takes the work
+ * items from a counter; jobs split into several groups are merged by a second kernel.
+ * Results land in each job's outputs exactly as knn_join would write them.          */
+knn_status knn_batch_launch(knn_batch* batch, void* stream);
+knn_status knn_batch_get_info(const knn_batch* batch, knn_batch_info* info);
+void knn_batch_destroy(knn_batch* batch);
+/* create (without a graph) + launch + synchronise + destroy                         */
+knn_status knn_join_batched(int32_t n_jobs, const knn_job* jobs, const knn_batch_opts* opts,
+                            void* stream);
+
+/* ------------------------------------------------------------------------------ */
 /* Learned start threshold (not in the paper: it generalises Section 4.4's           */
 /* MinPruneScore, a threshold derived from earlier work, to one predicted per query) */
 /* ------------------------------------------------------------------------------ */

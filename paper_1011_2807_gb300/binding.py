@@ -68,10 +68,15 @@ _lib = None
 _alloc_cbs = None
 
 
+_last_alloc_error = ""
+
+
 def _torch_alloc(nbytes, stream, ctx):
+    global _last_alloc_error
     try:
         return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
-    except Exception:
+    except Exception as e:   # reported by the library as KNN_ENOMEM
+        _last_alloc_error = repr(e)
         return None
 
 
@@ -110,7 +115,10 @@ def lib():
 
 def _check(L, status):
     if status != KNN_OK:
-        raise KnnError(status, L.knn_last_error().decode())
+        msg = L.knn_last_error().decode()
+        if status == KNN_ENOMEM and _last_alloc_error:
+            msg += f" (allocator: {_last_alloc_error})"
+        raise KnnError(status, msg)
 
 
 def knn_last_error() -> str:
@@ -482,3 +490,107 @@ def knn_join_learned(index: Index, model: "ThresholdModel | None", R, k: int, *,
                                  int(k), ctypes.byref(lo), out_ids.data_ptr(), out_scores.data_ptr(),
                                  ctypes.byref(st), _stream_ptr(stream)))
     return out_ids, out_scores, {"rows": int(st.rows), "fallback_rows": int(st.fallback_rows)}
+
+
+# ----------------------------------------------------------------------------------
+# batched joins
+# ----------------------------------------------------------------------------------
+
+class _Job(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_void_p), ("R", _Csr), ("k", ctypes.c_int32), ("out_ids", ctypes.c_void_p),
+                ("out_scores", ctypes.c_void_p)]
+
+
+class _BatchOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("threads", ctypes.c_int32), ("blocks_per_group", ctypes.c_int32),
+                ("level_margin", ctypes.c_float), ("use_graph", ctypes.c_int32),
+                ("skip_validation", ctypes.c_int32), ("stats", ctypes.c_void_p)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("work_items", ctypes.c_int64), ("ctas", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("shared_bytes", ctypes.c_int64), ("graph", ctypes.c_int32), ("kernels_per_launch", ctypes.c_int32)]
+
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        P = ctypes.POINTER
+        L.knn_batch_create.argtypes = [ctypes.c_int32, P(_Job), P(_BatchOpts), ctypes.c_void_p, P(ctypes.c_void_p)]
+        L.knn_batch_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.knn_batch_get_info.argtypes = [ctypes.c_void_p, P(_BatchInfo)]
+        L.knn_batch_destroy.argtypes = [ctypes.c_void_p]
+        L.knn_batch_destroy.restype = None
+        L.knn_join_batched.argtypes = [ctypes.c_int32, P(_Job), P(_BatchOpts), ctypes.c_void_p]
+        L._batch_ready = True
+    return L
+
+
+def _jobs_array(jobs, keep):
+    """jobs: list of (Index, DeviceCSR, k[, out_ids, out_scores]) -> ctypes array, outputs."""
+    arr = (_Job * len(jobs))()
+    outs = []
+    for i, jb in enumerate(jobs):
+        index, R, k = jb[0], jb[1], int(jb[2])
+        if not isinstance(R, DeviceCSR):
+            raise TypeError("batched jobs need DeviceCSR queries")
+        c = _csr(R, keep)
+        sdt = torch.int32 if index.dtype == KNN_U8 else torch.float32
+        if len(jb) > 3:
+            ids, sc = jb[3], jb[4]
+        else:
+            ids = torch.empty((c.n_rows, k), dtype=torch.int32, device="cuda")
+            sc = torch.empty((c.n_rows, k), dtype=sdt, device="cuda")
+        keep.extend([ids, sc])
+        arr[i] = _Job(index.handle, c, k, ids.data_ptr(), sc.data_ptr())
+        outs.append((ids, sc))
+    return arr, outs
+
+
+class Batch:
+    """A prepared knn_batch (work items, scratch, optionally a captured CUDA graph)."""
+
+    def __init__(self, jobs, *, mode="iiib", threads=0, blocks_per_group=0, level_margin=0.0, use_graph=True,
+                 skip_validation=False, stats: torch.Tensor | None = None, stream=None):
+        L = _batch_lib()
+        self._keep = []
+        arr, self.outputs = _jobs_array(jobs, self._keep)
+        self._keep.append(arr)
+        o = _BatchOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), int(blocks_per_group),
+                       float(level_margin), int(bool(use_graph)), int(bool(skip_validation)), _ptr(stats))
+        h = ctypes.c_void_p()
+        _check(L, L.knn_batch_create(len(jobs), arr, ctypes.byref(o), _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h.value
+
+    def launch(self, stream=None):
+        L = _batch_lib()
+        _check(L, L.knn_batch_launch(self._h, _stream_ptr(stream)))
+        return self.outputs
+
+    def info(self) -> dict:
+        L = _batch_lib()
+        inf = _BatchInfo()
+        _check(L, L.knn_batch_get_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in _BatchInfo._fields_}
+
+    def close(self):
+        if self._h:
+            _batch_lib().knn_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def knn_join_batched(jobs, *, mode="iiib", threads=0, blocks_per_group=0, level_margin=0.0, stream=None):
+    """Runs the jobs [(Index, DeviceCSR, k), ...] in one persistent launch; returns [(ids, scores)]."""
+    L = _batch_lib()
+    keep = []
+    arr, outs = _jobs_array(jobs, keep)
+    o = _BatchOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), int(blocks_per_group),
+                   float(level_margin), 0, 0, None)
+    _check(L, L.knn_join_batched(len(jobs), arr, ctypes.byref(o), _stream_ptr(stream)))
+    return outs

@@ -315,11 +315,11 @@ __device__ __forceinline__ typename JT<W>::Acc lookup_r(const int32_t* rf_d, con
     return (lo < n && rf_d[lo] == d) ? rf_w[lo] : (typename JT<W>::Acc)0;
 }
 
+// One query row against S blocks [b0, b1) of group g (the whole CTA).
 template <class W>
-__global__ void __launch_bounds__(1024) k_join(JoinParams p) {
+__device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row, const int g, unsigned char* smem) {
     using Acc = typename JT<W>::Acc;
     using Post = typename JT<W>::Post;
-    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ CtaState st;
     __shared__ double red_d[32];
     __shared__ unsigned long long red_u[32];
@@ -341,8 +341,6 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
 
     const int tid = threadIdx.x, T = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
-    const int64_t row = blockIdx.x / p.groups;
-    const int g = blockIdx.x - (int)(row * p.groups);
     const int64_t ra = p.r_indptr[row];
     const int rn = (int)(p.r_indptr[row + 1] - ra);
     const int b0 = p.groups == 1 ? p.block_begin : g * p.blocks_per_group;
@@ -747,6 +745,51 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     }
 }
 
+template <class W>
+__global__ void __launch_bounds__(1024) k_join(JoinParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int64_t row = blockIdx.x / p.groups;
+    const int g = blockIdx.x - (int)(row * p.groups);
+    join_row<W>(p, row, g, smem);
+}
+
+// ---------------------------------------------------------------------------------
+// batched form: many joins in one persistent launch
+// ---------------------------------------------------------------------------------
+struct BatchJob {
+    JoinParams p;          // this job's join (groups >= 1; one group reaches the outputs)
+    int64_t item_begin;    // its first work item; items are (group, row), group-major
+    int64_t n_items;
+};
+
+// Persistent CTAs take work items (job, S-block group, row) from one counter until it
+// runs out; items of one job and group run side by side, so that group's postings stay
+// in L2 while its rows read them, and later groups see the floors earlier ones set.
+template <class W>
+__global__ void __launch_bounds__(1024) k_join_batched(const BatchJob* __restrict__ jobs, int n_jobs,
+                                                       unsigned long long* __restrict__ head, int64_t total) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    for (;;) {
+        __syncthreads();   // the previous item is finished with shared memory
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(head, 1ull);
+        __syncthreads();
+        const long long it = s_item;
+        if (it >= total) break;
+        int lo = 0, hi = n_jobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].item_begin <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchJob& J = jobs[lo];
+        const int64_t local = it - J.item_begin;
+        const int g = (int)(local / J.p.n_rows);
+        const int64_t row = local - (int64_t)g * J.p.n_rows;
+        join_row<W>(J.p, row, g, smem);
+    }
+}
+
 // one CTA per row: top-k of the groups' lists
 __global__ void k_merge_groups(const u64* __restrict__ part, int64_t n_rows, int groups, int k, int P,
                                int32_t* out_ids, uint32_t* out_scores, int32_t* n_found) {
@@ -1073,5 +1116,278 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
         KNN_CUDA_TRY(cudaGetLastError());
         count_launch();
     }
+    return KNN_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// batched joins: a prepared plan (validated jobs, work items, scratch) whose launch
+// sequence -- reset the item counter, one persistent k_join_batched, one group merge
+// per job with several groups -- is captured once into a CUDA graph and replayed.
+// ---------------------------------------------------------------------------------
+struct knn_batch {
+    cudaStream_t cap_stream = nullptr;
+    knn::Buffers* bufs = nullptr;
+    knn_dtype dtype = KNN_U8;
+    int n_jobs = 0, T = 512, grid = 0;
+    size_t smem = 0;
+    int64_t total = 0;
+    knn::BatchJob* d_jobs = nullptr;
+    unsigned long long* d_head = nullptr;
+    knn::u64* floors = nullptr;
+    size_t floors_n = 0;
+    std::vector<knn::BatchJob> h_jobs;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int launches_per_run = 0;
+};
+
+namespace knn {
+
+static knn_status batch_enqueue(const knn_batch* b, cudaStream_t s) {
+    KNN_CUDA_TRY(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned long long), s));
+    if (b->floors_n) KNN_CUDA_TRY(cudaMemsetAsync(b->floors, 0, sizeof(u64) * b->floors_n, s));
+    if (b->dtype == KNN_U8)
+        k_join_batched<uint8_t><<<b->grid, b->T, b->smem, s>>>(b->d_jobs, b->n_jobs, b->d_head, b->total);
+    else
+        k_join_batched<float><<<b->grid, b->T, b->smem, s>>>(b->d_jobs, b->n_jobs, b->d_head, b->total);
+    KNN_CUDA_TRY(cudaGetLastError());
+    for (const BatchJob& J : b->h_jobs) {
+        if (J.p.groups <= 1 || J.p.n_rows == 0) continue;
+        int P = 2;
+        while (P < J.p.groups * J.p.k) P <<= 1;
+        k_merge_groups<<<(unsigned)J.p.n_rows, 256, P * 8, s>>>(J.p.part_keys, J.p.n_rows, J.p.groups, J.p.k, P,
+                                                                J.p.out_ids, (uint32_t*)J.p.out_scores, J.p.n_found);
+        KNN_CUDA_TRY(cudaGetLastError());
+    }
+    return KNN_OK;
+}
+
+}  // namespace knn
+
+extern "C" void knn_batch_destroy(knn_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->bufs) {
+        b->bufs->release();
+        delete b->bufs;
+    }
+    delete b;
+}
+
+extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, const knn_batch_opts* opts, void* stream_,
+                                       knn_batch** out) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!out) return fail(KNN_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_jobs < 1 || !jobs) return fail(KNN_EINVAL, "no jobs");
+    knn_batch_opts o = {};
+    if (opts) o = *opts;
+    if (o.mode != KNN_MODE_IIIB && o.mode != KNN_MODE_IIB) return fail(KNN_EINVAL, "unknown mode");
+    const float margin = o.level_margin > 0.0f ? o.level_margin : 0.25f;
+    if (!(margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
+    int dev = 0, smem_optin = 0, n_sm = 0;
+    KNN_CUDA_TRY(cudaGetDevice(&dev));
+    KNN_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    KNN_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+
+    knn_batch* b = new knn_batch();
+    b->bufs = new Buffers(stream);
+    auto bail = [&](knn_status st) {
+        knn_batch_destroy(b);
+        return st;
+    };
+    b->n_jobs = n_jobs;
+    b->dtype = jobs[0].index ? jobs[0].index->dtype : KNN_U8;
+    int T = o.threads ? o.threads : 512;
+    if (T < 64 || T > 1024 || (T & 31) || (T & (T - 1)))
+        return bail(fail(KNN_EINVAL, "threads must be a power of two in [64, 1024]"));
+    b->T = T;
+    const int bpg_opt = o.blocks_per_group > 0 ? o.blocks_per_group : 8;
+
+    Buffers tmp(stream);
+    std::vector<BatchJob> hj(n_jobs);
+    std::vector<double> cost(n_jobs);
+    size_t smem_max = 0;
+    for (int j = 0; j < n_jobs; j++) {
+        const knn_job& jb = jobs[j];
+        const knn_index* ix = jb.index;
+        if (!ix) return bail(fail(KNN_EINVAL, "job %d: index is NULL", j));
+        if (ix->dtype != b->dtype) return bail(fail(KNN_EINVAL, "job %d: all jobs must have the same dtype", j));
+        if (jb.k < 1) return bail(fail(KNN_EINVAL, "job %d: k must be >= 1", j));
+        if (jb.k > KNN_MAX_K) return bail(fail(KNN_EUNSUPPORTED, "job %d: k > %d", j, KNN_MAX_K));
+        if (jb.R.dim != ix->dim || jb.R.dtype != ix->dtype)
+            return bail(fail(KNN_EINVAL, "job %d: R does not match its index", j));
+        if (!jb.R.on_device) return bail(fail(KNN_EINVAL, "job %d: R must be in device memory", j));
+        DevCSR r;
+        knn_status st = prepare_csr(&jb.R, stream, tmp, !o.skip_validation, true, &r);
+        if (st != KNN_OK) return bail(fail(st, "job %d: %s", j, knn_last_error()));
+        if (r.n_rows > 0 && (!jb.out_ids || !jb.out_scores)) return bail(fail(KNN_EINVAL, "job %d: outputs are NULL", j));
+        if (ix->dtype == KNN_U8 && std::min(r.max_row_sum * ix->max_w, ix->max_row_sum * r.max_w) >= 2147483647.0)
+            return bail(fail(KNN_EUNSUPPORTED, "job %d: uint8 scores could overflow int32", j));
+        const int nb = ix->block_size;
+        if (T * 4 > nb || nb / (T * 4) > 16)
+            return bail(fail(KNN_EUNSUPPORTED, "job %d: S blocks of %d do not fit %d threads (need 4*T <= block <= 64*T)",
+                             j, nb, T));
+        const int max_r = std::max(1, r.max_row_nnz);
+        int rden_dim = 0;
+        if (ix->dtype == KNN_U8 && ix->dim <= 32768) {
+            const int rd = (int)((ix->dim + 15) & ~15);
+            if (smem_layout(nb, max_r, rd).total <= 110 * 1024) rden_dim = rd;
+        }
+        const size_t sm = smem_layout(nb, max_r, rden_dim).total;
+        if (sm + sizeof(CtaState) + 32 * 8 * 2 + 128 > (size_t)smem_optin)
+            return bail(fail(KNN_EUNSUPPORTED, "job %d: needs %zu bytes of shared memory", j, sm));
+        smem_max = std::max(smem_max, sm);
+        int bpg = std::min(bpg_opt, ix->n_blocks);
+        int groups = (int)ceil_div(ix->n_blocks, bpg);
+        while (groups * jb.k > 4096) {   // the group merge sorts groups * k keys in shared memory
+            bpg *= 2;
+            groups = (int)ceil_div(ix->n_blocks, bpg);
+        }
+        JoinParams& p = hj[j].p;
+        memset(&p, 0, sizeof(p));
+        p.n_rows = r.n_rows;
+        p.r_indptr = r.indptr;
+        p.r_idx = r.indices;
+        p.r_val = r.values;
+        p.n_s = ix->n_rows;
+        p.dim = ix->dim;
+        p.n_blocks = ix->n_blocks;
+        p.n_levels = ix->n_levels;
+        p.block_shift = ix->block_shift;
+        p.binoff = ix->binoff;
+        p.postings = ix->postings;
+        p.s_indptr = ix->s_indptr;
+        p.sp_d = ix->sp_d;
+        p.sp_w = ix->sp_w;
+        p.n_unidx = ix->n_unidx;
+        p.ubound = ix->ubound;
+        memcpy(p.levels, ix->levels, sizeof(p.levels));
+        p.k = jb.k;
+        p.groups = groups;
+        p.blocks_per_group = bpg;
+        p.block_begin = 0;
+        p.block_end = ix->n_blocks;
+        p.iiib = o.mode == KNN_MODE_IIIB && ix->n_levels > 1;
+        p.max_r_nnz = max_r;
+        p.rden_dim = rden_dim;
+        p.level_margin = margin;
+        p.out_ids = jb.out_ids;
+        p.out_scores = jb.out_scores;
+        p.stats = (unsigned long long*)o.stats;
+        hj[j].n_items = r.n_rows * groups;
+        // larger items first: a row's postings in one group grow with |S| / groups and nnz(r)
+        cost[j] = (double)ix->nnz / std::max(1, groups) * (double)(r.nnz + 1) / (double)std::max<int64_t>(1, r.n_rows);
+    }
+    // scratch: group lists and floors of jobs with several groups
+    for (int j = 0; j < n_jobs; j++) {
+        JoinParams& p = hj[j].p;
+        if (p.groups > 1 && p.n_rows > 0) {
+            knn_status st = b->bufs->get(&p.part_keys, (size_t)p.n_rows * p.groups * p.k);
+            if (st != KNN_OK) return bail(st);
+            b->floors_n += (size_t)p.n_rows;
+        }
+    }
+    if (b->floors_n) {
+        knn_status st = b->bufs->get(&b->floors, b->floors_n);
+        if (st != KNN_OK) return bail(st);
+        size_t off = 0;
+        for (int j = 0; j < n_jobs; j++)
+            if (hj[j].p.groups > 1 && hj[j].p.n_rows > 0) {
+                hj[j].p.floor_keys = b->floors + off;
+                off += (size_t)hj[j].p.n_rows;
+            }
+    }
+    std::vector<int> order(n_jobs);
+    for (int j = 0; j < n_jobs; j++) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    int64_t item = 0;
+    for (int j : order) {
+        hj[j].item_begin = item;
+        item += hj[j].n_items;
+        b->h_jobs.push_back(hj[j]);
+    }
+    b->total = item;
+    b->smem = smem_max;
+    knn_status st;
+    if ((st = b->bufs->get(&b->d_jobs, (size_t)n_jobs)) != KNN_OK) return bail(st);
+    if ((st = b->bufs->get(&b->d_head, 1)) != KNN_OK) return bail(st);
+#define BATCH_CUDA(expr)                                                                  \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess) return bail(fail(KNN_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_))); \
+    } while (0)
+    BATCH_CUDA(cudaMemcpyAsync(b->d_jobs, b->h_jobs.data(), sizeof(BatchJob) * n_jobs, cudaMemcpyHostToDevice, stream));
+    int per_sm = 0;
+    if (b->dtype == KNN_U8) {
+        BATCH_CUDA(cudaFuncSetAttribute(k_join_batched<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+        BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_join_batched<uint8_t>, T, b->smem));
+    } else {
+        BATCH_CUDA(cudaFuncSetAttribute(k_join_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+        BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_join_batched<float>, T, b->smem));
+    }
+    if (per_sm < 1) return bail(fail(KNN_EUNSUPPORTED, "the batched kernel does not fit an SM"));
+    b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, std::max<int64_t>(1, b->total)));
+    BATCH_CUDA(cudaFuncSetAttribute(k_merge_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 8));
+    b->launches_per_run = 1;
+    for (const BatchJob& J : b->h_jobs) b->launches_per_run += (J.p.groups > 1 && J.p.n_rows > 0) ? 1 : 0;
+    BATCH_CUDA(cudaStreamSynchronize(stream));
+    tmp.release();
+    if (o.use_graph) {
+        BATCH_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+        BATCH_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        st = batch_enqueue(b, b->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+        if (st != KNN_OK) {
+            if (g) cudaGraphDestroy(g);
+            return bail(st);
+        }
+        if (e != cudaSuccess) return bail(fail(KNN_ECUDA, "graph capture: %s", cudaGetErrorString(e)));
+        b->graph = g;
+        BATCH_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    }
+#undef BATCH_CUDA
+    *out = b;
+    return KNN_OK;
+}
+
+extern "C" knn_status knn_batch_launch(knn_batch* b, void* stream_) {
+    if (!b) return fail(KNN_EINVAL, "batch is NULL");
+    cudaStream_t s = (cudaStream_t)stream_;
+    if (b->total == 0) return KNN_OK;
+    if (b->exec) {
+        KNN_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+    } else {
+        KNN_TRY(batch_enqueue(b, s));
+    }
+    count_launch(b->launches_per_run);
+    return KNN_OK;
+}
+
+extern "C" knn_status knn_batch_get_info(const knn_batch* b, knn_batch_info* info) {
+    if (!b || !info) return fail(KNN_EINVAL, "NULL argument");
+    info->work_items = b->total;
+    info->ctas = b->grid;
+    info->threads = b->T;
+    info->shared_bytes = (int64_t)b->smem;
+    info->graph = b->exec != nullptr;
+    info->kernels_per_launch = b->launches_per_run;
+    return KNN_OK;
+}
+
+extern "C" knn_status knn_join_batched(int32_t n_jobs, const knn_job* jobs, const knn_batch_opts* opts, void* stream) {
+    knn_batch_opts o = {};
+    if (opts) o = *opts;
+    o.use_graph = 0;
+    knn_batch* b = nullptr;
+    KNN_TRY(knn_batch_create(n_jobs, jobs, &o, stream, &b));
+    knn_status st = knn_batch_launch(b, stream);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    knn_batch_destroy(b);
+    if (st != KNN_OK) return st;
+    if (e != cudaSuccess) return fail(KNN_ECUDA, "batched join: %s", cudaGetErrorString(e));
     return KNN_OK;
 }

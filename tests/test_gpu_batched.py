@@ -1,0 +1,117 @@
+"""The batched form: many joins in one persistent launch (optionally a CUDA graph)
+return exactly what separate knn_join calls return."""
+import numpy as np
+import pytest
+
+from paper_1011_2807_gb300 import synth
+import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def knn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1011_2807_gb300 as knn
+    knn.lib()
+    return knn
+
+
+@pytest.fixture(scope="module")
+def jobs(knn):
+    rng = np.random.default_rng(44)
+    out = []
+    for j in range(9):
+        n_s = int(rng.choice([3000, 9000, 20000, 45000]))
+        n_r = int(rng.choice([0, 1, 40, 300, 2500])) if j else 0
+        k = int(rng.choice([1, 5, 10, 20, 50]))
+        S = synth.spectrum_u8(n_s, 500 + j, role="S")
+        R = synth.spectrum_u8(n_r, 600 + j, role="R")
+        idx = knn.knn_join_build_index(S, block_size=int(rng.choice([2048, 4096, 16384])))
+        out.append(dict(S=S, R=R, k=k, idx=idx, Rd=knn.DeviceCSR.from_host(R)))
+    yield out
+    for j in out:
+        j["idx"].close()
+
+
+def reference(knn, jobs):
+    import torch
+    res = []
+    for j in jobs:
+        ids, sc = knn.knn_join(j["idx"], j["Rd"], j["k"])
+        res.append((ids.cpu(), sc.cpu()))
+    torch.cuda.synchronize()
+    return res
+
+
+@pytest.mark.parametrize("bpg", [0, 1, 3, 100])
+def test_batched_equals_separate_joins(knn, jobs, bpg):
+    ref = reference(knn, jobs)
+    outs = knn.knn_join_batched([(j["idx"], j["Rd"], j["k"]) for j in jobs], blocks_per_group=bpg)
+    for (ids, sc), (rid, rsc) in zip(outs, ref):
+        assert np.array_equal(ids.cpu().numpy(), rid.numpy())
+        assert np.array_equal(sc.cpu().numpy(), rsc.numpy())
+
+
+def test_batched_against_oracle(knn, jobs, oracle_mod):
+    outs = knn.knn_join_batched([(j["idx"], j["Rd"], j["k"]) for j in jobs])
+    for j, (ids, sc) in zip(jobs[:5], outs[:5]):
+        eids, esc, _ = oracle_mod.iib_join(j["R"], j["S"], j["k"], threads=8)
+        compare.assert_exact(ids.cpu().numpy(), sc.cpu().numpy(), eids, esc, "batched")
+
+
+def test_graph_replay(knn, jobs):
+    import torch
+    ref = reference(knn, jobs)
+    b = knn.Batch([(j["idx"], j["Rd"], j["k"]) for j in jobs], use_graph=True)
+    info = b.info()
+    assert info["graph"] == 1 and info["work_items"] > 0
+    for _ in range(3):
+        for ids, sc in b.outputs:
+            ids.fill_(-5)
+        outs = b.launch()
+        torch.cuda.synchronize()
+        for (ids, sc), (rid, rsc) in zip(outs, ref):
+            assert np.array_equal(ids.cpu().numpy(), rid.numpy())
+            assert np.array_equal(sc.cpu().numpy(), rsc.numpy())
+    # new query contents of the same shape: a replay joins the new contents
+    j = jobs[3]
+    R2 = synth.spectrum_u8(j["R"].n_rows, 777, role="R", nnz=np.diff(j["R"].indptr))
+    j["Rd"].indices.copy_(knn.DeviceCSR.from_host(R2).indices)
+    j["Rd"].values.copy_(knn.DeviceCSR.from_host(R2).values)
+    outs = b.launch()
+    torch.cuda.synchronize()
+    rid, rsc = knn.knn_join(j["idx"], j["Rd"], j["k"])
+    assert np.array_equal(outs[3][0].cpu().numpy(), rid.cpu().numpy())
+    b.close()
+
+
+def test_batched_float_jobs(knn, oracle_mod):
+    js = []
+    for j in range(3):
+        S = synth.uniform_f32(4000 + 1000 * j, 800, 5, 40, 900 + j)
+        R = synth.uniform_f32(50, 800, 5, 40, 950 + j)
+        js.append((S, R, 10, knn.knn_join_build_index(S, block_size=2048)))
+    outs = knn.knn_join_batched([(idx, knn.DeviceCSR.from_host(R), k) for S, R, k, idx in js])
+    for (S, R, k, idx), (ids, sc) in zip(js, outs):
+        eids, esc, _ = oracle_mod.iib_join(R, S, k, threads=8)
+        compare.assert_close(R, S, list(range(R.n_rows)), ids.cpu().numpy(), sc.cpu().numpy(), eids, esc,
+                             what="batched f32")
+        idx.close()
+
+
+def test_batched_errors(knn, jobs):
+    from paper_1011_2807_gb300.binding import KNN_EINVAL, KNN_EUNSUPPORTED, KnnError
+    S = synth.uniform_f32(3000, 10000, 5, 40, 991)
+    fidx = knn.knn_join_build_index(S)
+    R = synth.uniform_f32(10, 10000, 5, 40, 992)
+    with pytest.raises(KnnError) as e:      # mixed dtypes
+        knn.knn_join_batched([(jobs[0]["idx"], jobs[0]["Rd"], 5), (fidx, knn.DeviceCSR.from_host(R), 5)])
+    assert e.value.status == KNN_EINVAL
+    with pytest.raises(KnnError) as e:      # a 256-vector S block cannot feed 512 threads
+        tiny = knn.knn_join_build_index(synth.spectrum_u8(200, 993, role="S"), block_size=256)
+        knn.knn_join_batched([(tiny, jobs[1]["Rd"], 5)])
+    assert e.value.status == KNN_EUNSUPPORTED
+    fidx.close()
