@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -54,6 +55,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-oracle sample time")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--n-train", type=int, default=20000, help="training queries of the learned threshold")
+    ap.add_argument("--batch-jobs", type=int, default=64)
     return ap.parse_args()
 
 
@@ -220,6 +225,122 @@ def run_reference(args):
 # our arm
 # ----------------------------------------------------------------------------------
 
+def time_events(fn, reps):
+    import torch
+    ms = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def batched_leg(args, R, S, reps):
+    """64 uneven joins (config-3 sizes; S = leading rows of the benchmark's S, R = windows
+    of its R) as one persistent launch replayed from a CUDA graph, against the same
+    joins as 64 separate knn_join calls.  Block sizes are autotuned per |S| class."""
+    import torch
+    import paper_1011_2807_gb300 as knn
+    from paper_1011_2807_gb300 import autotune, synth
+    spec = synth.config3_jobs(args.batch_jobs)
+    t0 = time.perf_counter()
+    tuned = {}
+    jobs = []
+    for j, js in enumerate(spec):
+        n_s = min(js["n_s"], S.n_rows)
+        n_r = min(js["n_r"], R.n_rows)
+        o = (j * 7919) % max(1, R.n_rows - n_r + 1)
+        Sj = S.slice_rows(0, n_s)
+        Rj = R.slice_rows(o, o + n_r)
+        key = round(math.log2(max(2, n_s)))
+        if key not in tuned:
+            tuned[key] = autotune.tune(Sj, Rj.slice_rows(0, min(256, n_r)), js["k"], threads=512, reps=1,
+                                       max_trials=12)
+        cfg = tuned[key]
+        idx = knn.knn_join_build_index(Sj, block_size=cfg["block_size"])
+        jobs.append(dict(idx=idx, Rd=knn.DeviceCSR.from_host(Rj), k=js["k"], n_r=n_r, n_s=n_s,
+                         bpl=cfg["blocks_per_launch"]))
+    setup_s = time.perf_counter() - t0
+    for jb in jobs:   # validate every R once
+        knn.knn_join(jb["idx"], jb["Rd"], jb["k"])
+    torch.cuda.synchronize()
+    ref = []
+
+    def run_plain():
+        ref.clear()
+        for jb in jobs:
+            ref.append(knn.knn_join(jb["idx"], jb["Rd"], jb["k"], skip_validation=True,
+                                    blocks_per_launch=jb["bpl"]))
+
+    run_plain()
+    torch.cuda.synchronize()
+    plain_ms = time_events(run_plain, reps)
+    b = knn.Batch([(jb["idx"], jb["Rd"], jb["k"]) for jb in jobs], use_graph=True, threads=512,
+                  skip_validation=True)
+    b.launch()
+    torch.cuda.synchronize()
+    launches0 = knn.knn_kernel_launch_count()
+    batched_ms = time_events(lambda: b.launch(), reps)
+    launches = (knn.knn_kernel_launch_count() - launches0) // max(1, reps)
+    identical = all(torch.equal(a[0], c[0]) and torch.equal(a[1], c[1]) for a, c in zip(b.outputs, ref))
+    rows = sum(jb["n_r"] for jb in jobs)
+    info = b.info()
+    b.close()
+    for jb in jobs:
+        jb["idx"].close()
+    return {"jobs": len(jobs), "rows": rows, "plain_ms": plain_ms, "batched_ms": batched_ms,
+            "plain_rows_per_s": rows / (plain_ms / 1e3), "batched_rows_per_s": rows / (batched_ms / 1e3),
+            "speedup": plain_ms / batched_ms, "identical": identical, "graph": bool(info["graph"]),
+            "work_items": info["work_items"], "kernels_per_launch": launches, "setup_s": setup_s,
+            "autotuned_block_sizes": sorted({v["block_size"] for v in tuned.values()}),
+            "workload": "config-3 sizes: |R| log-U[100, 50k], |S| log-U[1e4, 1e6], k in {1,5,10,20,50}; "
+                        "S = leading rows of the benchmark S, R = windows of the benchmark R"}
+
+
+def learned_leg(args, R, S, idx, Rd, ids, sc, plain_ms, reps):
+    """Learned start threshold: train on exact k-th scores of fresh queries from the same
+    generator, then join the benchmark R from the predictions (verify-and-fallback)."""
+    import torch
+    import paper_1011_2807_gb300 as knn
+    from paper_1011_2807_gb300 import synth
+    k = args.k
+    t0 = time.perf_counter()
+    T = synth.spectrum_u8(args.n_train, synth.config_seed(2, "train"), role="R")
+    Td = knn.DeviceCSR.from_host(T)
+    _, tsc = knn.knn_join(idx, Td, k)
+    labels = tsc[:, k - 1].float()
+    model = knn.ThresholdModel(seed=1)
+    t1 = time.perf_counter()
+    loss = model.train(Td, labels, epochs=15, batch=512, quantile=0.1, seed=1)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    label_s = t1 - t0
+    lids = torch.empty_like(ids)
+    lsc = torch.empty_like(sc)
+    st = {}
+
+    def run():
+        st.update(knn.knn_join_learned(idx, model, Rd, k, out_ids=lids, out_scores=lsc)[2])
+
+    run()
+    torch.cuda.synchronize()
+    learned_ms = time_events(run, reps)
+    identical = torch.equal(lids, ids) and torch.equal(lsc, sc)
+    c_l = torch.zeros(1, dtype=torch.int64, device="cuda")
+    knn.knn_join_learned(idx, model, Rd, k, postings_scanned=c_l, out_ids=lids, out_scores=lsc)
+    torch.cuda.synchronize()
+    model.close()
+    return {"rows_per_s": R.n_rows / (learned_ms / 1e3), "plain_rows_per_s": R.n_rows / (plain_ms / 1e3),
+            "speedup": plain_ms / learned_ms, "identical": identical,
+            "fallback_rate": st.get("fallback_rows", 0) / max(1, R.n_rows),
+            "postings_scanned": int(c_l.item()), "train_queries": T.n_rows, "train_s": train_s,
+            "label_join_s": label_s, "final_loss": loss, "quantile": 0.1}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -335,6 +456,12 @@ def run_ours(args):
     if traffic_note:
         roofline["traffic_note"] = traffic_note
 
+    batched = learned = None
+    if rank == 0 and world == 1 and not args.no_learned:
+        learned = learned_leg(args, R, S, idx, Rd, ids, sc, kern_ms, reps=3)
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = batched_leg(args, R, S, reps=3)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, dt = cpu_oracle_rows_per_s(R, S, k, args.cpu_seconds)
@@ -357,7 +484,7 @@ def run_ours(args):
                            "timed_calls": "knn_join on device-resident R, validated once before timing",
                            "parallelism": f"R rows split over {world} GPU(s), index replicated"},
                 "gpu_launches": launches, "roofline": roofline, "clocks": clk,
-                "e2e": e2e, "cpu_baseline": cpu,
+                "e2e": e2e, "cpu_baseline": cpu, "learned_vs_plain": learned, "batched_vs_plain": batched,
                 "kernel_ms_per_step": kern_ms}
         print(json.dumps(line), flush=True)
     idx.close()

@@ -115,3 +115,14 @@ def test_batched_errors(knn, jobs):
         knn.knn_join_batched([(tiny, jobs[1]["Rd"], 5)])
     assert e.value.status == KNN_EUNSUPPORTED
     fidx.close()
+
+
+def test_autotune_picks_a_valid_config(knn, tmp_path, monkeypatch):
+    from paper_1011_2807_gb300 import autotune
+    monkeypatch.setenv("KNN_TUNE_CACHE", str(tmp_path / "tune.json"))
+    S = synth.spectrum_u8(30000, 1201, role="S")
+    R = synth.spectrum_u8(100, 1202, role="R")
+    best = autotune.tune(S, R, 5, threads=512, reps=1, max_trials=6)
+    assert 4 * best["threads"] <= best["block_size"] <= 64 * best["threads"] and best["ms"] > 0
+    got = autotune.lookup(S.n_rows, R.n_rows, R.nnz / R.n_rows, 5, "u8")
+    assert got["block_size"] == best["block_size"]
