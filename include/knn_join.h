@@ -208,11 +208,16 @@ typedef struct {
     knn_mode mode;
     int32_t threads;            /* threads per CTA for every job, power of two; 0 = 512.
                                    Every job's S block must lie in [4*threads, 64*threads]. */
-    int32_t blocks_per_group;   /* S blocks per work item; 0 = 8                             */
+    int32_t blocks_per_group;   /* S blocks per work item; 0 = 16                            */
     float level_margin;         /* as in knn_join_opts (0 = 0.25)                            */
     int32_t use_graph;          /* knn_batch_create: capture the launch into a CUDA graph   */
     int32_t skip_validation;    /* 1: trust every R                                          */
     int64_t* stats;             /* device int64[KNN_STATS_LEN] or NULL (all jobs together)   */
+    int64_t wait_spins;         /* bound of a work item's wait for its row's previous group,
+                                   in ~128 ns sleeps (0 = 2^24); past it the item gives up and
+                                   knn_batch_check reports KNN_ETIMEOUT                        */
+    int32_t test_never_publish; /* test hook: groups never announce completion, so every wait
+                                   runs out (exercises the timeout path without a fault)      */
 } knn_batch_opts;
 
 typedef struct knn_batch knn_batch;   /* a prepared batch (validated jobs, work items, scratch) */
@@ -233,9 +238,14 @@ typedef struct {
 knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, const knn_batch_opts* opts,
                             void* stream, knn_batch** out);
 /* Runs every job (asynchronously on `stream`): one persistent kernel takes the work
- * items from a counter; jobs split into several groups are merged by a second kernel.
- * Results land in each job's outputs exactly as knn_join would write them.          */
+ * items from a counter, in order; a row's group g starts from the top-k its group g-1
+ * left (a bounded wait if that item is still running).  Results land in each job's
+ * outputs exactly as knn_join would write them.                                     */
 knn_status knn_batch_launch(knn_batch* batch, void* stream);
+/* Synchronises `stream` and reports the last run: KNN_ETIMEOUT if a work item gave up
+ * its bounded wait for the previous S-block group of its row (its outputs are then
+ * incomplete), else KNN_OK.                                                         */
+knn_status knn_batch_check(const knn_batch* batch, void* stream);
 knn_status knn_batch_get_info(const knn_batch* batch, knn_batch_info* info);
 void knn_batch_destroy(knn_batch* batch);
 /* create (without a graph) + launch + synchronise + destroy                         */

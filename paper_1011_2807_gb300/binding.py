@@ -504,7 +504,8 @@ class _Job(ctypes.Structure):
 class _BatchOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("threads", ctypes.c_int32), ("blocks_per_group", ctypes.c_int32),
                 ("level_margin", ctypes.c_float), ("use_graph", ctypes.c_int32),
-                ("skip_validation", ctypes.c_int32), ("stats", ctypes.c_void_p)]
+                ("skip_validation", ctypes.c_int32), ("stats", ctypes.c_void_p), ("wait_spins", ctypes.c_int64),
+                ("test_never_publish", ctypes.c_int32)]
 
 
 class _BatchInfo(ctypes.Structure):
@@ -519,6 +520,7 @@ def _batch_lib():
         L.knn_batch_create.argtypes = [ctypes.c_int32, P(_Job), P(_BatchOpts), ctypes.c_void_p, P(ctypes.c_void_p)]
         L.knn_batch_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.knn_batch_get_info.argtypes = [ctypes.c_void_p, P(_BatchInfo)]
+        L.knn_batch_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.knn_batch_destroy.argtypes = [ctypes.c_void_p]
         L.knn_batch_destroy.restype = None
         L.knn_join_batched.argtypes = [ctypes.c_int32, P(_Job), P(_BatchOpts), ctypes.c_void_p]
@@ -551,13 +553,15 @@ class Batch:
     """A prepared knn_batch (work items, scratch, optionally a captured CUDA graph)."""
 
     def __init__(self, jobs, *, mode="iiib", threads=0, blocks_per_group=0, level_margin=0.0, use_graph=True,
-                 skip_validation=False, stats: torch.Tensor | None = None, stream=None):
+                 skip_validation=False, stats: torch.Tensor | None = None, wait_spins: int = 0,
+                 test_never_publish: bool = False, stream=None):
         L = _batch_lib()
         self._keep = []
         arr, self.outputs = _jobs_array(jobs, self._keep)
         self._keep.append(arr)
         o = _BatchOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), int(blocks_per_group),
-                       float(level_margin), int(bool(use_graph)), int(bool(skip_validation)), _ptr(stats))
+                       float(level_margin), int(bool(use_graph)), int(bool(skip_validation)), _ptr(stats),
+                       int(wait_spins), int(bool(test_never_publish)))
         h = ctypes.c_void_p()
         _check(L, L.knn_batch_create(len(jobs), arr, ctypes.byref(o), _stream_ptr(stream), ctypes.byref(h)))
         self._h = h.value
@@ -566,6 +570,11 @@ class Batch:
         L = _batch_lib()
         _check(L, L.knn_batch_launch(self._h, _stream_ptr(stream)))
         return self.outputs
+
+    def check(self, stream=None):
+        """Synchronises and raises KnnError (KNN_ETIMEOUT) if a bounded wait gave up."""
+        L = _batch_lib()
+        _check(L, L.knn_batch_check(self._h, _stream_ptr(stream)))
 
     def info(self) -> dict:
         L = _batch_lib()
@@ -591,6 +600,6 @@ def knn_join_batched(jobs, *, mode="iiib", threads=0, blocks_per_group=0, level_
     keep = []
     arr, outs = _jobs_array(jobs, keep)
     o = _BatchOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), int(blocks_per_group),
-                   float(level_margin), 0, 0, None)
+                   float(level_margin), 0, 0, None, 0, 0)
     _check(L, L.knn_join_batched(len(jobs), arr, ctypes.byref(o), _stream_ptr(stream)))
     return outs

@@ -143,6 +143,7 @@ struct JoinParams {
     // [block_begin, block_end) of every row; rows carry their top-k keys between launches
     int32_t block_begin, block_end, carry_in, carry_out;
     u64* carry;
+    int32_t* done;   // batched form: per row, the number of groups finished
 };
 
 struct SmemLayout {
@@ -316,8 +317,14 @@ __device__ __forceinline__ typename JT<W>::Acc lookup_r(const int32_t* rf_d, con
 }
 
 // One query row against S blocks [b0, b1) of group g (the whole CTA).
+// out_mode: OUT_FINAL writes ids/scores, OUT_CARRY the row's keys to p.carry for the
+// next range of S blocks, OUT_GROUP the group's keys to p.part_keys (merged later).
+enum { OUT_FINAL = 0, OUT_CARRY = 1, OUT_GROUP = 2 };
+
 template <class W>
-__device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row, const int g, unsigned char* smem) {
+__device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row, const int g, const int b0,
+                                         const int b1, const bool carry_in, const int out_mode,
+                                         unsigned char* smem) {
     using Acc = typename JT<W>::Acc;
     using Post = typename JT<W>::Post;
     __shared__ CtaState st;
@@ -343,8 +350,6 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
     const int64_t ra = p.r_indptr[row];
     const int rn = (int)(p.r_indptr[row + 1] - ra);
-    const int b0 = p.groups == 1 ? p.block_begin : g * p.blocks_per_group;
-    const int b1 = p.groups == 1 ? p.block_end : min(p.n_blocks, b0 + p.blocks_per_group);
 
     // load r (ascending d) and its largest weight
     double mloc = 0.0;
@@ -377,8 +382,8 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         st.pred_level = -1;
         for (int l = 0; l < p.n_levels; l++) st.lbnd[l] = l ? JT<W>::level_bound(m, p.levels[l]) : 0.0;
     }
-    if (p.carry_in) {   // the row's top-k from the blocks of earlier launches
-        for (int q = tid; q < p.k; q += T) topk[q] = p.carry[row * p.k + q];
+    if (carry_in) {   // the row's top-k from the earlier S blocks
+        for (int q = tid; q < p.k; q += T) topk[q] = __ldcg(p.carry + row * p.k + q);
         __syncthreads();
         if (tid == 0) {
             int n = 0;
@@ -714,9 +719,9 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     }
 
     // ---- output ----
-    if (p.carry_out) {
+    if (out_mode == OUT_CARRY) {
         for (int q = tid; q < p.k; q += T) p.carry[row * p.k + q] = q < st.size ? topk[q] : 0ull;
-    } else if (p.groups == 1) {
+    } else if (out_mode == OUT_FINAL) {
         for (int q = tid; q < p.k; q += T) {
             u64 key = q < st.size ? topk[q] : 0ull;
             int64_t o = row * p.k + q;
@@ -750,43 +755,86 @@ __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int64_t row = blockIdx.x / p.groups;
     const int g = blockIdx.x - (int)(row * p.groups);
-    join_row<W>(p, row, g, smem);
+    if (p.groups == 1)
+        join_row<W>(p, row, 0, p.block_begin, p.block_end, p.carry_in != 0, p.carry_out ? OUT_CARRY : OUT_FINAL,
+                     smem);
+    else
+        join_row<W>(p, row, g, g * p.blocks_per_group, min(p.n_blocks, (g + 1) * p.blocks_per_group), false,
+                    OUT_GROUP, smem);
 }
 
 // ---------------------------------------------------------------------------------
 // batched form: many joins in one persistent launch
 // ---------------------------------------------------------------------------------
-struct BatchJob {
-    JoinParams p;          // this job's join (groups >= 1; one group reaches the outputs)
-    int64_t item_begin;    // its first work item; items are (group, row), group-major
-    int64_t n_items;
+constexpr int BATCH_MAX_JOBS = 64;   // jobs per launch (their parameters are kernel parameters)
+
+struct BatchParams {
+    JoinParams p[BATCH_MAX_JOBS];               // each job's join (groups >= 1)
+    long long item_begin[BATCH_MAX_JOBS + 1];   // first work item of each job; items are (group, row)
+    int n_jobs;
 };
+static_assert(sizeof(BatchParams) < 32000, "batch parameters must fit the kernel parameter space");
 
 // Persistent CTAs take work items (job, S-block group, row) from one counter until it
 // runs out; items of one job and group run side by side, so that group's postings stay
-// in L2 while its rows read them, and later groups see the floors earlier ones set.
+// in L2 while its rows read them, and each row's top-k is carried from group to group.
+constexpr long long BATCH_WAIT_SPINS = 1LL << 24;   // default bound: x ~128 ns sleeps, a few seconds
 template <class W>
-__global__ void __launch_bounds__(1024) k_join_batched(const BatchJob* __restrict__ jobs, int n_jobs,
-                                                       unsigned long long* __restrict__ head, int64_t total) {
+__global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ BatchParams bp,
+                                                       unsigned long long* __restrict__ head,
+                                                       unsigned* __restrict__ err, long long wait_spins,
+                                                       int no_publish) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
+    __shared__ bool s_ok;
+    const long long total = bp.item_begin[bp.n_jobs];
     for (;;) {
         __syncthreads();   // the previous item is finished with shared memory
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(head, 1ull);
         __syncthreads();
         const long long it = s_item;
         if (it >= total) break;
-        int lo = 0, hi = n_jobs - 1;
+        int lo = 0, hi = bp.n_jobs - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (jobs[mid].item_begin <= it) lo = mid;
+            if (bp.item_begin[mid] <= it) lo = mid;
             else hi = mid - 1;
         }
-        const BatchJob& J = jobs[lo];
-        const int64_t local = it - J.item_begin;
-        const int g = (int)(local / J.p.n_rows);
-        const int64_t row = local - (int64_t)g * J.p.n_rows;
-        join_row<W>(J.p, row, g, smem);
+        const JoinParams& J = bp.p[lo];
+        const int64_t local = it - bp.item_begin[lo];
+        const int g = (int)(local / J.n_rows);
+        const int64_t row = local - (int64_t)g * J.n_rows;
+        // group g continues from group g-1's top-k of this row: that item was taken
+        // earlier (items are handed out in order), so it is running or done; wait for
+        // it with a bounded spin, and give up with an error flag rather than hang
+        if (g > 0 && threadIdx.x == 0) {
+            int* dp = J.done + row;
+            long long spins = 0;
+            int v = 0;
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(dp) : "memory");
+                if (v >= g || v < 0) break;   // ready, or an earlier group of this row failed
+                if (++spins > wait_spins) break;
+                __nanosleep(128);
+            }
+            s_ok = v >= g;
+            if (!s_ok) {
+                atomicOr(err, 1u);
+                atomicExch(dp, -1);   // later groups of this row give up at once
+            }
+        }
+        __syncthreads();
+        if (g > 0 && !s_ok) continue;
+        const bool last = g == J.groups - 1;
+        join_row<W>(J, row, g, g * J.blocks_per_group, min(J.n_blocks, (g + 1) * J.blocks_per_group), g > 0,
+                    last ? OUT_FINAL : OUT_CARRY, smem);
+        if (!last && !no_publish) {   // publish: the carried keys are in global memory before the flag
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(J.done + row), "r"(g + 1) : "memory");
+            }
+        }
     }
 }
 
@@ -1131,11 +1179,14 @@ struct knn_batch {
     int n_jobs = 0, T = 512, grid = 0;
     size_t smem = 0;
     int64_t total = 0;
-    knn::BatchJob* d_jobs = nullptr;
-    unsigned long long* d_head = nullptr;
-    knn::u64* floors = nullptr;
-    size_t floors_n = 0;
-    std::vector<knn::BatchJob> h_jobs;
+    std::vector<knn::BatchParams> chunks;   // up to BATCH_MAX_JOBS jobs per launch
+    unsigned long long* d_head = nullptr;   // one work counter per chunk
+    unsigned* d_err = nullptr;     // set when a bounded wait gave up
+    int32_t* done = nullptr;       // per row of every multi-group job: groups finished
+    size_t done_n = 0;
+    long long wait_spins = 0;
+    int no_publish = 0;
+    int64_t n_items_all = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int launches_per_run = 0;
@@ -1144,19 +1195,18 @@ struct knn_batch {
 namespace knn {
 
 static knn_status batch_enqueue(const knn_batch* b, cudaStream_t s) {
-    KNN_CUDA_TRY(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned long long), s));
-    if (b->floors_n) KNN_CUDA_TRY(cudaMemsetAsync(b->floors, 0, sizeof(u64) * b->floors_n, s));
-    if (b->dtype == KNN_U8)
-        k_join_batched<uint8_t><<<b->grid, b->T, b->smem, s>>>(b->d_jobs, b->n_jobs, b->d_head, b->total);
-    else
-        k_join_batched<float><<<b->grid, b->T, b->smem, s>>>(b->d_jobs, b->n_jobs, b->d_head, b->total);
-    KNN_CUDA_TRY(cudaGetLastError());
-    for (const BatchJob& J : b->h_jobs) {
-        if (J.p.groups <= 1 || J.p.n_rows == 0) continue;
-        int P = 2;
-        while (P < J.p.groups * J.p.k) P <<= 1;
-        k_merge_groups<<<(unsigned)J.p.n_rows, 256, P * 8, s>>>(J.p.part_keys, J.p.n_rows, J.p.groups, J.p.k, P,
-                                                                J.p.out_ids, (uint32_t*)J.p.out_scores, J.p.n_found);
+    KNN_CUDA_TRY(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned long long) * b->chunks.size(), s));
+    KNN_CUDA_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), s));
+    if (b->done_n) KNN_CUDA_TRY(cudaMemsetAsync(b->done, 0, sizeof(int32_t) * b->done_n, s));
+    for (size_t c = 0; c < b->chunks.size(); c++) {
+        const BatchParams& bp = b->chunks[c];
+        if (bp.item_begin[bp.n_jobs] == 0) continue;
+        if (b->dtype == KNN_U8)
+            k_join_batched<uint8_t><<<b->grid, b->T, b->smem, s>>>(bp, b->d_head + c, b->d_err, b->wait_spins,
+                                                                   b->no_publish);
+        else
+            k_join_batched<float><<<b->grid, b->T, b->smem, s>>>(bp, b->d_head + c, b->d_err, b->wait_spins,
+                                                                 b->no_publish);
         KNN_CUDA_TRY(cudaGetLastError());
     }
     return KNN_OK;
@@ -1200,14 +1250,20 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
     };
     b->n_jobs = n_jobs;
     b->dtype = jobs[0].index ? jobs[0].index->dtype : KNN_U8;
+    b->wait_spins = o.wait_spins > 0 ? o.wait_spins : BATCH_WAIT_SPINS;
+    b->no_publish = o.test_never_publish ? 1 : 0;
     int T = o.threads ? o.threads : 512;
     if (T < 64 || T > 1024 || (T & 31) || (T & (T - 1)))
         return bail(fail(KNN_EINVAL, "threads must be a power of two in [64, 1024]"));
     b->T = T;
-    const int bpg_opt = o.blocks_per_group > 0 ? o.blocks_per_group : 8;
+    const int bpg_opt = o.blocks_per_group > 0 ? o.blocks_per_group : 16;
 
     Buffers tmp(stream);
-    std::vector<BatchJob> hj(n_jobs);
+    struct JobPlan {
+        JoinParams p;
+        int64_t n_items;
+    };
+    std::vector<JobPlan> hj(n_jobs);
     std::vector<double> cost(n_jobs);
     size_t smem_max = 0;
     for (int j = 0; j < n_jobs; j++) {
@@ -1242,10 +1298,7 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
         smem_max = std::max(smem_max, sm);
         int bpg = std::min(bpg_opt, ix->n_blocks);
         int groups = (int)ceil_div(ix->n_blocks, bpg);
-        while (groups * jb.k > 4096) {   // the group merge sorts groups * k keys in shared memory
-            bpg *= 2;
-            groups = (int)ceil_div(ix->n_blocks, bpg);
-        }
+
         JoinParams& p = hj[j].p;
         memset(&p, 0, sizeof(p));
         p.n_rows = r.n_rows;
@@ -1281,45 +1334,52 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
         // larger items first: a row's postings in one group grow with |S| / groups and nnz(r)
         cost[j] = (double)ix->nnz / std::max(1, groups) * (double)(r.nnz + 1) / (double)std::max<int64_t>(1, r.n_rows);
     }
-    // scratch: group lists and floors of jobs with several groups
+    // scratch of jobs with several groups: each row's carried keys and finished groups
     for (int j = 0; j < n_jobs; j++) {
         JoinParams& p = hj[j].p;
         if (p.groups > 1 && p.n_rows > 0) {
-            knn_status st = b->bufs->get(&p.part_keys, (size_t)p.n_rows * p.groups * p.k);
+            knn_status st = b->bufs->get(&p.carry, (size_t)p.n_rows * p.k);
             if (st != KNN_OK) return bail(st);
-            b->floors_n += (size_t)p.n_rows;
+            b->done_n += (size_t)p.n_rows;
         }
     }
-    if (b->floors_n) {
-        knn_status st = b->bufs->get(&b->floors, b->floors_n);
+    if (b->done_n) {
+        knn_status st = b->bufs->get(&b->done, b->done_n);
         if (st != KNN_OK) return bail(st);
         size_t off = 0;
         for (int j = 0; j < n_jobs; j++)
             if (hj[j].p.groups > 1 && hj[j].p.n_rows > 0) {
-                hj[j].p.floor_keys = b->floors + off;
+                hj[j].p.done = b->done + off;
                 off += (size_t)hj[j].p.n_rows;
             }
     }
     std::vector<int> order(n_jobs);
     for (int j = 0; j < n_jobs; j++) order[j] = j;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-    int64_t item = 0;
-    for (int j : order) {
-        hj[j].item_begin = item;
-        item += hj[j].n_items;
-        b->h_jobs.push_back(hj[j]);
+    for (size_t i = 0; i < order.size(); i += BATCH_MAX_JOBS) {
+        BatchParams bp;
+        memset(&bp, 0, sizeof(bp));
+        long long item = 0;
+        for (size_t q = i; q < std::min(order.size(), i + BATCH_MAX_JOBS); q++) {
+            bp.p[bp.n_jobs] = hj[order[q]].p;
+            bp.item_begin[bp.n_jobs] = item;
+            item += hj[order[q]].n_items;
+            bp.n_jobs++;
+        }
+        bp.item_begin[bp.n_jobs] = item;
+        b->chunks.push_back(bp);
+        b->n_items_all += item;
     }
-    b->total = item;
+    b->total = b->n_items_all;
     b->smem = smem_max;
     knn_status st;
-    if ((st = b->bufs->get(&b->d_jobs, (size_t)n_jobs)) != KNN_OK) return bail(st);
-    if ((st = b->bufs->get(&b->d_head, 1)) != KNN_OK) return bail(st);
+    if ((st = b->bufs->get(&b->d_head, b->chunks.size())) != KNN_OK) return bail(st);
+    if ((st = b->bufs->get(&b->d_err, 1)) != KNN_OK) return bail(st);
 #define BATCH_CUDA(expr)                                                                  \
     do {                                                                                  \
         cudaError_t e_ = (expr);                                                          \
         if (e_ != cudaSuccess) return bail(fail(KNN_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_))); \
     } while (0)
-    BATCH_CUDA(cudaMemcpyAsync(b->d_jobs, b->h_jobs.data(), sizeof(BatchJob) * n_jobs, cudaMemcpyHostToDevice, stream));
     int per_sm = 0;
     if (b->dtype == KNN_U8) {
         BATCH_CUDA(cudaFuncSetAttribute(k_join_batched<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
@@ -1330,9 +1390,7 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
     }
     if (per_sm < 1) return bail(fail(KNN_EUNSUPPORTED, "the batched kernel does not fit an SM"));
     b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, std::max<int64_t>(1, b->total)));
-    BATCH_CUDA(cudaFuncSetAttribute(k_merge_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 8));
-    b->launches_per_run = 1;
-    for (const BatchJob& J : b->h_jobs) b->launches_per_run += (J.p.groups > 1 && J.p.n_rows > 0) ? 1 : 0;
+    b->launches_per_run = (int)b->chunks.size();
     BATCH_CUDA(cudaStreamSynchronize(stream));
     tmp.release();
     if (o.use_graph) {
@@ -1367,6 +1425,15 @@ extern "C" knn_status knn_batch_launch(knn_batch* b, void* stream_) {
     return KNN_OK;
 }
 
+extern "C" knn_status knn_batch_check(const knn_batch* b, void* stream_) {
+    if (!b) return fail(KNN_EINVAL, "batch is NULL");
+    unsigned e = 0;
+    KNN_CUDA_TRY(cudaMemcpyAsync(&e, b->d_err, sizeof(e), cudaMemcpyDeviceToHost, (cudaStream_t)stream_));
+    KNN_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream_));
+    if (e) return fail(KNN_ETIMEOUT, "a batched work item waited too long for its row's previous group");
+    return KNN_OK;
+}
+
 extern "C" knn_status knn_batch_get_info(const knn_batch* b, knn_batch_info* info) {
     if (!b || !info) return fail(KNN_EINVAL, "NULL argument");
     info->work_items = b->total;
@@ -1385,9 +1452,7 @@ extern "C" knn_status knn_join_batched(int32_t n_jobs, const knn_job* jobs, cons
     knn_batch* b = nullptr;
     KNN_TRY(knn_batch_create(n_jobs, jobs, &o, stream, &b));
     knn_status st = knn_batch_launch(b, stream);
-    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (st == KNN_OK) st = knn_batch_check(b, stream);
     knn_batch_destroy(b);
-    if (st != KNN_OK) return st;
-    if (e != cudaSuccess) return fail(KNN_ECUDA, "batched join: %s", cudaGetErrorString(e));
-    return KNN_OK;
+    return st;
 }

@@ -126,3 +126,25 @@ def test_autotune_picks_a_valid_config(knn, tmp_path, monkeypatch):
     assert 4 * best["threads"] <= best["block_size"] <= 64 * best["threads"] and best["ms"] > 0
     got = autotune.lookup(S.n_rows, R.n_rows, R.nnz / R.n_rows, 5, "u8")
     assert got["block_size"] == best["block_size"]
+
+
+def test_bounded_wait_reports_timeout(knn, jobs):
+    """A work item that waits for a flag nothing sets gives up after its bounded spin and
+    the host reads KNN_ETIMEOUT; the GPU context stays usable afterwards."""
+    import torch
+    from paper_1011_2807_gb300.binding import KNN_ETIMEOUT, KnnError
+    multi = [j for j in jobs if j["idx"].info()["n_blocks"] > 1 and j["R"].n_rows > 0]
+    assert multi
+    j = multi[0]
+    b = knn.Batch([(j["idx"], j["Rd"], j["k"])], use_graph=False, blocks_per_group=1, wait_spins=200,
+                  test_never_publish=True)
+    b.launch()
+    with pytest.raises(KnnError) as e:
+        b.check()
+    assert e.value.status == KNN_ETIMEOUT
+    b.close()
+    # the context still works: a normal batch afterwards is exact
+    ids, sc = knn.knn_join(j["idx"], j["Rd"], j["k"])
+    (bids, bsc), = knn.knn_join_batched([(j["idx"], j["Rd"], j["k"])], blocks_per_group=1)
+    torch.cuda.synchronize()
+    assert torch.equal(ids, bids) and torch.equal(sc, bsc)
