@@ -67,11 +67,33 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def rank_seed(rank: int) -> int:
+    """Query seed of one rank: every rank joins its own rows (weak scaling)."""
+    from paper_1011_2807_gb300 import synth
+    return synth.config_seed(2, "R") + 7919 * rank
+
+
 def workload(args, rank):
     from paper_1011_2807_gb300 import synth
     S = synth.spectrum_u8(args.n_s, synth.config_seed(2, "S"), role="S")
-    R = synth.spectrum_u8(args.n_r, synth.config_seed(2, "R") + 7919 * rank, role="R")
+    R = synth.spectrum_u8(args.n_r, rank_seed(rank), role="R")
     return R, S
+
+
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The slowest rank's value (timings are taken as the max over ranks)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rows_per_s(rows_per_rank: int, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: the rows all ranks joined over the slowest rank's time."""
+    return rows_per_rank * world * steps / (max_ms / 1000.0)
 
 
 def workload_name(args):
@@ -398,14 +420,9 @@ def run_ours(args):
     launches = knn.knn_kernel_launch_count() - launches0
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    rows_total = R.n_rows * world * args.steps
-    value = rows_total / (ms / 1000.0)
+    value = job_rows_per_s(R.n_rows, world, args.steps, ms)
 
     # end to end through the public call with host buffers (pinned)
     e2e = None
@@ -424,11 +441,7 @@ def run_ours(args):
         for _ in range(args.steps):
             knn.knn_join(idx, Rh, k, mode=args.mode, threads=args.threads, out_ids=hid, out_scores=hsc,
                          outputs_on_host=True)
-        dt = time.perf_counter() - t
-        if world > 1:
-            tt = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
+        dt = max_over_ranks(time.perf_counter() - t, world)
         h2d = int(R.indptr.nbytes + R.indices.nbytes + R.values.nbytes)
         d2h = int(hid.numel() * 4 + hsc.numel() * 4)
         e2e = {"value": R.n_rows * world * args.steps / dt, "unit": UNIT,
