@@ -108,7 +108,7 @@ knn_status check_device_csr_into(const knn_csr* in, void* scratch, bool validate
 }  // namespace knn
 
 struct knn_index {
-    int64_t n_rows = 0, nnz = 0;
+    int64_t n_rows = 0, nnz = 0, n_postings = 0;   // n_postings: nnz + list padding
     int32_t dim = 0, block_size = 0, n_blocks = 0, n_levels = 0, block_shift = 0;
     knn_dtype dtype = KNN_U8;
     int32_t max_row_nnz = 0;
@@ -116,7 +116,8 @@ struct knn_index {
     float levels[KNN_MAX_LEVELS] = {};  // ladder of bound thresholds, levels[0] == 0
     // device arrays
     uint32_t* binoff = nullptr;  // [n_blocks * dim * n_levels + 1] posting-bin offsets
-    void* postings = nullptr;    // [nnz] u32 (lid | w<<16) for u8; uint2 {lid, w} for f32
+    void* postings = nullptr;    // [n_postings] u32 (lid | w<<16) for u8; uint2 {lid, w} for f32;
+                                 // every (S block, d) list padded to whole 16-byte chunks
     int64_t* s_indptr = nullptr; // [n_rows + 1]
     int32_t* sp_d = nullptr;     // [nnz] features of each s in cut order (dimension)
     void* sp_w = nullptr;        // [nnz] weights in the same order (u8 or f32)

@@ -163,6 +163,18 @@ __global__ void k_bin_count(const int64_t* __restrict__ indptr, const int32_t* _
     }
 }
 
+// Pads every (S block, d) list to a whole number of 16-byte chunks: the padding is
+// added to the list's last bin (bucket 0), so lists start on chunk boundaries and the
+// whole-list prefix ends on one.  Padding postings are zero (local id 0, weight 0).
+__global__ void k_pad_lists(uint32_t* __restrict__ cnt, int64_t n_lists, int32_t n_levels, uint32_t per_chunk) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_lists) return;
+    uint32_t* c = cnt + i * n_levels;
+    uint32_t t = 0;
+    for (int l = 0; l < n_levels; l++) t += c[l];
+    c[n_levels - 1] += (per_chunk - t % per_chunk) % per_chunk;
+}
+
 template <class W>
 __global__ void k_scatter(const int64_t* __restrict__ indptr, const int32_t* __restrict__ sp_d,
                           const W* __restrict__ sp_w, const uint8_t* __restrict__ bucket, BinParams p,
@@ -248,18 +260,21 @@ extern "C" knn_status knn_join_build_index(const knn_csr* S, const knn_build_opt
     const size_t wsz = s.dtype == KNN_U8 ? 1 : 4;
     const size_t psz = s.dtype == KNN_U8 ? 4 : 8;
     const size_t nbins = (size_t)ix->n_blocks * (size_t)s.dim * (size_t)nl;
+    {   // posting offsets are 32-bit: nnz plus at most (16 / psz - 1) padding postings per list
+        const uint64_t lists = (uint64_t)ix->n_blocks * (uint64_t)s.dim;
+        const uint64_t pad = (uint64_t)(16 / psz - 1) * std::min<uint64_t>(lists, (uint64_t)s.nnz);
+        if ((uint64_t)s.nnz + pad > 0xffffffffull)
+            return bail(fail(KNN_EUNSUPPORTED, "S has too many nonzeros for 32-bit posting offsets"));
+    }
     uint8_t* spw = nullptr;
     uint8_t* post = nullptr;
     knn_status st;
     if ((st = ix->bufs->get(&ix->binoff, nbins + 1)) != KNN_OK) return bail(st);
-    // +16 bytes: the join reads whole aligned 16-byte vectors at list ends
-    if ((st = ix->bufs->get(&post, (size_t)s.nnz * psz + 16)) != KNN_OK) return bail(st);
     if ((st = ix->bufs->get(&ix->s_indptr, (size_t)s.n_rows + 1)) != KNN_OK) return bail(st);
     if ((st = ix->bufs->get(&ix->sp_d, (size_t)s.nnz)) != KNN_OK) return bail(st);
     if ((st = ix->bufs->get(&spw, (size_t)s.nnz * wsz)) != KNN_OK) return bail(st);
     if ((st = ix->bufs->get(&ix->n_unidx, (size_t)nl * s.n_rows)) != KNN_OK) return bail(st);
     if ((st = ix->bufs->get(&ix->ubound, (size_t)nl * s.n_rows)) != KNN_OK) return bail(st);
-    ix->postings = post;
     ix->sp_w = spw;
 
     uint32_t* df = nullptr;
@@ -316,8 +331,21 @@ extern "C" knn_status knn_join_build_index(const knn_csr* S, const knn_build_opt
         BAIL_CUDA(cudaGetLastError());
         count_launch();
     }
+    {
+        const int64_t n_lists = (int64_t)ix->n_blocks * s.dim;
+        k_pad_lists<<<launch_blocks(n_lists, 256), 256, 0, stream>>>(ix->binoff, n_lists, nl, (uint32_t)(16 / psz));
+        BAIL_CUDA(cudaGetLastError());
+        count_launch();
+    }
     if ((st = exclusive_scan_u32(ix->binoff, ix->binoff, (int64_t)nbins, stream, tmp)) != KNN_OK) return bail(st);
     BAIL_CUDA(cudaMemcpyAsync(cursor, ix->binoff, sizeof(uint32_t) * (nbins + 1), cudaMemcpyDeviceToDevice, stream));
+    uint32_t n_post = 0;
+    BAIL_CUDA(cudaMemcpyAsync(&n_post, ix->binoff + nbins, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    BAIL_CUDA(cudaStreamSynchronize(stream));
+    ix->n_postings = n_post;
+    if ((st = ix->bufs->get(&post, (size_t)n_post * psz)) != KNN_OK) return bail(st);
+    BAIL_CUDA(cudaMemsetAsync(post, 0, (size_t)n_post * psz, stream));   // padding postings: id 0, weight 0
+    ix->postings = post;
     if (s.n_rows) {
         if (s.dtype == KNN_U8)
             k_scatter<uint8_t><<<wblocks, 256, 0, stream>>>(ix->s_indptr, ix->sp_d, (const uint8_t*)spw, bucket,

@@ -202,7 +202,6 @@ struct CtaState {
     int32_t cmin_i;
     double lbnd[KNN_MAX_LEVELS];  // residual bound of every level for this row
     unsigned long long n_steps, n_merges, n_rounds;  // work counters (thread 0)
-    int next_list;  // next list of r to hand to a warp in the scan
     int qcnt;       // entries in the completion queue
     int pred_level; // level the next block's list ranges were prefetched for (-1: none)
     // radix select of a candidate threshold (blocks with too many candidates)
@@ -321,7 +320,7 @@ __device__ __forceinline__ typename JT<W>::Acc lookup_r(const int32_t* rf_d, con
 // next range of S blocks, OUT_GROUP the group's keys to p.part_keys (merged later).
 enum { OUT_FINAL = 0, OUT_CARRY = 1, OUT_GROUP = 2 };
 
-template <class W>
+template <class W, bool COUNT>
 __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row, const int g, const int b0,
                                          const int b1, const bool carry_in, const int out_mode,
                                          unsigned char* smem) {
@@ -399,7 +398,15 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     const int chunks = nb / (T * 4);  // <= 16 by construction (mask has 64 bits)
 
     for (int b = (rn > 0 ? b0 : b1); b < b1; b++) {
-        // ---- 1. threshold and level (warp 0: lane l tests level l) ----
+        // ---- 1. level, list ranges and work items (warp 0) ----
+        // Lane l tests level l.  This block's list ranges were requested (cp.async) during
+        // the previous block for the level that block used; they are loaded again only if
+        // the level changed.  The lists (each starting on a 16-byte chunk) are then cut
+        // into work items of at most CH chunks, and the next block's ranges requested.
+        constexpr int V = JT<W>::PER_VEC;   // postings per 16-byte chunk
+        constexpr int G = 8, U = 4, CH = G * U;
+        uint32_t* lbeg = lbeg_buf + (b & 1) * p.max_r_nnz;
+        uint32_t* lend = lend_buf + (b & 1) * p.max_r_nnz;
         if (warp == 0) {
             u64 fl = st.floor;
             if (p.floor_keys) {
@@ -414,62 +421,71 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                 ok = lb < theta && lb <= p.level_margin * theta;
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
+            const int level = m ? 31 - __clz(m) : 0;
+            const int pred = st.pred_level;
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncwarp();
+            if (pred != level) {
+                const size_t bbase = (size_t)b * (size_t)p.dim;
+                for (int i = lane; i < rn; i += 32) {
+                    size_t base = (bbase + (size_t)rf_d[i]) * (size_t)p.n_levels;
+                    lbeg[i] = p.binoff[base];
+                    lend[i] = p.binoff[base + (size_t)(p.n_levels - level)];
+                }
+            }
+            __syncwarp();
+            // work items: exclusive prefix of ceil(chunks / CH) over the lists
+            const int per = (rn + 31) / 32;
+            const int a0 = min(rn, lane * per), a1 = min(rn, a0 + per);
+            uint32_t sum = 0;
+            for (int i = a0; i < a1; i++) {
+                const uint32_t nch = (lend[i] - lbeg[i] + V - 1) / V;
+                const uint32_t it = (nch + CH - 1) / CH;
+                ipre[i] = it;
+                sum += it;
+            }
+            uint32_t x = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            uint32_t run = x - sum;
+            for (int i = a0; i < a1; i++) {
+                const uint32_t c = ipre[i];
+                ipre[i] = run;
+                run += c;
+            }
+            if (lane == 31) ipre[rn] = x;
+            if (b + 1 < b1) {   // next block's ranges, assuming the level stays
+                uint32_t* nbeg = lbeg_buf + ((b + 1) & 1) * p.max_r_nnz;
+                uint32_t* nend = lend_buf + ((b + 1) & 1) * p.max_r_nnz;
+                const size_t nbase = (size_t)(b + 1) * (size_t)p.dim;
+                for (int i = lane; i < rn; i += 32) {
+                    size_t base = (nbase + (size_t)rf_d[i]) * (size_t)p.n_levels;
+                    cp_async4(nbeg + i, p.binoff + base);
+                    cp_async4(nend + i, p.binoff + base + (size_t)(p.n_levels - level));
+                }
+                cp_async_commit();
+            }
             if (lane == 0) {
-                const int level = m ? 31 - __clz(m) : 0;
-                st.next_list = nwarps;   // list counter of this block's scan
                 st.floor = fl;
                 st.theta = theta;
                 st.level = level;
+                st.pending = 0;
                 st.n_steps++;
                 st.lb = st.lbnd[level];
+                st.pred_level = b + 1 < b1 ? level : -1;
                 JT<W>::set_cmin(st, JT<W>::cheap_min(theta, st.lb));
             }
         }
         __syncthreads();
         const int level = st.level;
-        // ---- list ranges of r's features in block b at this level ----
-        // They were requested (cp.async) during the previous block's scan for the level
-        // that block used; if the level changed, or this is the first block, load now.
-        constexpr int V = JT<W>::PER_VEC;   // postings per 16-byte chunk
-        uint32_t* lbeg = lbeg_buf + (b & 1) * p.max_r_nnz;
-        uint32_t* lend = lend_buf + (b & 1) * p.max_r_nnz;
-        const int pred = st.pred_level;
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        if (pred != level) {
-            const size_t bbase = (size_t)b * (size_t)p.dim;
-            for (int i = tid; i < rn; i += T) {
-                size_t base = (bbase + (size_t)rf_d[i]) * (size_t)p.n_levels;
-                lbeg[i] = p.binoff[base];
-                lend[i] = p.binoff[base + (size_t)(p.n_levels - level)];
-            }
-        }
-        __syncthreads();
-        if (tid == 0) st.pred_level = b + 1 < b1 ? level : -1;   // read before the barrier above
-        if (b + 1 < b1) {   // next block's ranges, assuming the level stays
-            uint32_t* nbeg = lbeg_buf + ((b + 1) & 1) * p.max_r_nnz;
-            uint32_t* nend = lend_buf + ((b + 1) & 1) * p.max_r_nnz;
-            const size_t nbase = (size_t)(b + 1) * (size_t)p.dim;
-            for (int i = tid; i < rn; i += T) {
-                size_t base = (nbase + (size_t)rf_d[i]) * (size_t)p.n_levels;
-                cp_async4(nbeg + i, p.binoff + base);
-                cp_async4(nend + i, p.binoff + base + (size_t)(p.n_levels - level));
-            }
-            cp_async_commit();
-        }
         // ---- 2. scan: acc[lid] += r[d] * w over the indexed prefixes ----
-        // The lists' 16-byte chunks are cut into work items of at most CH chunks (an item
-        // never spans two lists).  Each 8-lane sub-warp takes an equal contiguous range
-        // of items, so every sub-warp runs the same number of iterations; per item each
-        // lane loads U chunks (one 128-byte line per sub-warp per load) before adding.
+        // Each 8-lane sub-warp takes an equal contiguous range of work items, so every
+        // sub-warp runs the same number of iterations; per item each lane loads U chunks
+        // (one 128-byte line per sub-warp per load) before adding.  Only the last chunk
+        // of a prefix can be partial (lists start on chunk boundaries).
         {
-            constexpr int G = 8, U = 4, CH = G * U;
-            for (int i = tid; i < rn; i += T) {
-                const uint32_t bg = lbeg[i], en = lend[i];
-                const uint32_t nch = en > bg ? (en + V - 1) / V - bg / V : 0u;
-                ipre[i] = (nch + CH - 1) / CH;
-            }
-            __syncthreads();
-            cta_exclusive_scan(ipre, rn, (uint32_t*)red_u);
             const Post* post = (const Post*)p.postings;
             const int nsub = T / G, sub = tid / G, sl = tid % G;
             const uint32_t total = ipre[rn];
@@ -487,28 +503,28 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
             }
             for (uint32_t I = I0; I < I1; I++) {
                 while (ipre[li + 1] <= I) li++;
-                const uint32_t bg = lbeg[li], en = lend[li];
+                const uint32_t en = lend[li];
                 const Acc rw = rf_w[li];
-                const uint32_t cf = bg / V, cend = (en + V - 1) / V;
-                const uint32_t c0 = cf + (I - ipre[li]) * CH;
-                const uint32_t c1 = min(cend, c0 + CH);
-                if (sl == 0) n_post += min(c1 * V, en) - max(c0 * V, bg);
+                const uint32_t p0 = lbeg[li] + (I - ipre[li]) * (CH * V);   // first posting of the item
+                const Post* base = post + p0;
                 uint4 v[U];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    const uint32_t c = c0 + sl + G * u;
-                    if (c < c1) v[u] = *(const uint4*)(post + (size_t)c * V);
+                    const uint32_t q = p0 + (uint32_t)(sl + G * u) * V;
+                    if (q < en) v[u] = *(const uint4*)(base + (sl + G * u) * V);
                 }
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    const uint32_t c = c0 + sl + G * u;
-                    if (c < c1) {
+                    const uint32_t q = p0 + (uint32_t)(sl + G * u) * V;
+                    if (q < en) {
                         const Post* e = (const Post*)&v[u];
-                        const uint32_t p0 = c * V;
+                        const uint32_t nv = min((uint32_t)V, en - q);
 #pragma unroll
                         for (int j = 0; j < V; j++) {
-                            if (p0 + j >= bg && p0 + j < en)
+                            if (j < (int)nv) {
                                 red_add_shared(acc_s + 4u * (uint32_t)JT<W>::post_lid(e[j]), rw * JT<W>::post_w(e[j]));
+                                if (COUNT) n_post += JT<W>::post_w(e[j]) != (Acc)0;   // padding has weight 0
+                            }
                         }
                     }
                 }
@@ -545,14 +561,9 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         // total candidates of the block
         int wsum = mycount;
         for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-        if (lane == 0) red_u[warp] = (unsigned long long)wsum;
+        if (lane == 0 && wsum) atomicAdd(&st.pending, wsum);
         __syncthreads();
-        if (tid == 0) {
-            unsigned long long t = 0;
-            for (int w = 0; w < nwarps; w++) t += red_u[w];
-            st.pending = (int)t;
-        }
-        __syncthreads();
+        if (st.pending > 0) {   // most blocks, once the threshold has settled, have none
         if (st.pending > PUSH_CAP) {
             // Too many candidates for one merge (typically the first block, where the
             // threshold is still 0).  Radix-select, on the candidates' partial scores,
@@ -713,6 +724,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
             if (!more) break;
             if (tid == 0) st.n_rounds++;
         }
+        }   // st.pending > 0
         // publish this group's k-th key as a floor for the other groups of the row
         if (tid == 0 && p.floor_keys && st.size == p.k) atomicMax(p.floor_keys + row, st.kth);
         __syncthreads();
@@ -750,18 +762,27 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     }
 }
 
-template <class W>
+template <class W, bool COUNT>
 __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int64_t row = blockIdx.x / p.groups;
     const int g = blockIdx.x - (int)(row * p.groups);
     if (p.groups == 1)
-        join_row<W>(p, row, 0, p.block_begin, p.block_end, p.carry_in != 0, p.carry_out ? OUT_CARRY : OUT_FINAL,
-                     smem);
+        join_row<W, COUNT>(p, row, 0, p.block_begin, p.block_end, p.carry_in != 0,
+                           p.carry_out ? OUT_CARRY : OUT_FINAL, smem);
     else
-        join_row<W>(p, row, g, g * p.blocks_per_group, min(p.n_blocks, (g + 1) * p.blocks_per_group), false,
-                    OUT_GROUP, smem);
+        join_row<W, COUNT>(p, row, g, g * p.blocks_per_group, min(p.n_blocks, (g + 1) * p.blocks_per_group), false,
+                           OUT_GROUP, smem);
 }
+
+// The posting count (stats, eq. 4 checks) costs a compare per posting, so it is
+// compiled into a separate instance that runs only when a counter is requested.
+using JoinKernel = void (*)(JoinParams);
+static JoinKernel join_kernel(knn_dtype dt, bool count) {
+    if (dt == KNN_U8) return count ? k_join<uint8_t, true> : k_join<uint8_t, false>;
+    return count ? k_join<float, true> : k_join<float, false>;
+}
+
 
 // ---------------------------------------------------------------------------------
 // batched form: many joins in one persistent launch
@@ -779,7 +800,7 @@ static_assert(sizeof(BatchParams) < 32000, "batch parameters must fit the kernel
 // runs out; items of one job and group run side by side, so that group's postings stay
 // in L2 while its rows read them, and each row's top-k is carried from group to group.
 constexpr long long BATCH_WAIT_SPINS = 1LL << 24;   // default bound: x ~128 ns sleeps, a few seconds
-template <class W>
+template <class W, bool COUNT>
 __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ BatchParams bp,
                                                        unsigned long long* __restrict__ head,
                                                        unsigned* __restrict__ err, long long wait_spins,
@@ -826,8 +847,8 @@ __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ B
         __syncthreads();
         if (g > 0 && !s_ok) continue;
         const bool last = g == J.groups - 1;
-        join_row<W>(J, row, g, g * J.blocks_per_group, min(J.n_blocks, (g + 1) * J.blocks_per_group), g > 0,
-                    last ? OUT_FINAL : OUT_CARRY, smem);
+        join_row<W, COUNT>(J, row, g, g * J.blocks_per_group, min(J.n_blocks, (g + 1) * J.blocks_per_group),
+                           g > 0, last ? OUT_FINAL : OUT_CARRY, smem);
         if (!last && !no_publish) {   // publish: the carried keys are in global memory before the flag
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -836,6 +857,12 @@ __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ B
             }
         }
     }
+}
+
+using BatchKernel = void (*)(const BatchParams, unsigned long long*, unsigned*, long long, int);
+static BatchKernel batch_kernel(knn_dtype dt, bool count) {
+    if (dt == KNN_U8) return count ? k_join_batched<uint8_t, true> : k_join_batched<uint8_t, false>;
+    return count ? k_join_batched<float, true> : k_join_batched<float, false>;
 }
 
 // one CTA per row: top-k of the groups' lists
@@ -971,10 +998,8 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
         KNN_CUDA_TRY(cudaMemsetAsync(p.floor_keys, 0, sizeof(u64) * r.n_rows, stream));
     }
     int64_t grid = r.n_rows * groups;
-    if (ix->dtype == KNN_U8)
-        KNN_CUDA_TRY(cudaFuncSetAttribute(k_join<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-    else
-        KNN_CUDA_TRY(cudaFuncSetAttribute(k_join<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    const JoinKernel kern = join_kernel(ix->dtype, p.touched || p.stats);
+    KNN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     // One group per row: S-block-synchronous launches.  Every launch walks all rows over
     // the same few S blocks, so their postings stay in L2 while all rows read them.
     int per_launch = groups == 1 ? (o.blocks_per_launch > 0 ? o.blocks_per_launch : 8) : ix->n_blocks;
@@ -986,10 +1011,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
         p.block_end = std::min(ix->n_blocks, (li + 1) * per_launch);
         p.carry_in = li > 0;
         p.carry_out = li + 1 < n_launch;
-        if (ix->dtype == KNN_U8)
-            k_join<uint8_t><<<(unsigned)grid, T, L.total, stream>>>(p);
-        else
-            k_join<float><<<(unsigned)grid, T, L.total, stream>>>(p);
+        kern<<<(unsigned)grid, T, L.total, stream>>>(p);
         KNN_CUDA_TRY(cudaGetLastError());
         count_launch();
     }
@@ -1146,10 +1168,8 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     if (!(p.level_margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     p.carry = (u64*)((unsigned char*)scratch + NOALLOC_HEADER);
 
-    if (ix->dtype == KNN_U8)
-        KNN_CUDA_TRY(cudaFuncSetAttribute(k_join<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-    else
-        KNN_CUDA_TRY(cudaFuncSetAttribute(k_join<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    const JoinKernel kern = join_kernel(ix->dtype, p.touched || p.stats);
+    KNN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     const int per_launch = std::min(ix->n_blocks, o.blocks_per_launch > 0 ? o.blocks_per_launch : 8);
     const int n_launch = (int)ceil_div(ix->n_blocks, per_launch);
     for (int li = 0; li < n_launch; li++) {
@@ -1157,10 +1177,7 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
         p.block_end = std::min(ix->n_blocks, (li + 1) * per_launch);
         p.carry_in = li > 0;
         p.carry_out = li + 1 < n_launch;
-        if (ix->dtype == KNN_U8)
-            k_join<uint8_t><<<(unsigned)r.n_rows, T, L.total, stream>>>(p);
-        else
-            k_join<float><<<(unsigned)r.n_rows, T, L.total, stream>>>(p);
+        kern<<<(unsigned)r.n_rows, T, L.total, stream>>>(p);
         KNN_CUDA_TRY(cudaGetLastError());
         count_launch();
     }
@@ -1186,6 +1203,7 @@ struct knn_batch {
     size_t done_n = 0;
     long long wait_spins = 0;
     int no_publish = 0;
+    bool count = false;            // stats requested: the posting-counting kernel instance
     int64_t n_items_all = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1201,12 +1219,8 @@ static knn_status batch_enqueue(const knn_batch* b, cudaStream_t s) {
     for (size_t c = 0; c < b->chunks.size(); c++) {
         const BatchParams& bp = b->chunks[c];
         if (bp.item_begin[bp.n_jobs] == 0) continue;
-        if (b->dtype == KNN_U8)
-            k_join_batched<uint8_t><<<b->grid, b->T, b->smem, s>>>(bp, b->d_head + c, b->d_err, b->wait_spins,
-                                                                   b->no_publish);
-        else
-            k_join_batched<float><<<b->grid, b->T, b->smem, s>>>(bp, b->d_head + c, b->d_err, b->wait_spins,
-                                                                 b->no_publish);
+        batch_kernel(b->dtype, b->count)<<<b->grid, b->T, b->smem, s>>>(bp, b->d_head + c, b->d_err, b->wait_spins,
+                                                                         b->no_publish);
         KNN_CUDA_TRY(cudaGetLastError());
     }
     return KNN_OK;
@@ -1381,13 +1395,10 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
         if (e_ != cudaSuccess) return bail(fail(KNN_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_))); \
     } while (0)
     int per_sm = 0;
-    if (b->dtype == KNN_U8) {
-        BATCH_CUDA(cudaFuncSetAttribute(k_join_batched<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-        BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_join_batched<uint8_t>, T, b->smem));
-    } else {
-        BATCH_CUDA(cudaFuncSetAttribute(k_join_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-        BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_join_batched<float>, T, b->smem));
-    }
+    b->count = o.stats != nullptr;
+    const BatchKernel kern = batch_kernel(b->dtype, b->count);
+    BATCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, b->smem));
     if (per_sm < 1) return bail(fail(KNN_EUNSUPPORTED, "the batched kernel does not fit an SM"));
     b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, std::max<int64_t>(1, b->total)));
     b->launches_per_run = (int)b->chunks.size();
