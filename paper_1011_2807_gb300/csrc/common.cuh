@@ -116,7 +116,7 @@ struct knn_index {
     float levels[KNN_MAX_LEVELS] = {};  // ladder of bound thresholds, levels[0] == 0
     // device arrays
     uint32_t* binoff = nullptr;  // [n_blocks * dim * n_levels + 1] posting-bin offsets
-    void* postings = nullptr;    // [n_postings] u32 (lid | w<<16) for u8; uint2 {lid, w} for f32;
+    void* postings = nullptr;    // [n_postings] u32 (lid | w<<24) for u8; uint2 {lid, w} for f32;
                                  // every (S block, d) list padded to whole 16-byte chunks
     int64_t* s_indptr = nullptr; // [n_rows + 1]
     int32_t* sp_d = nullptr;     // [nnz] features of each s in cut order (dimension)

@@ -19,7 +19,8 @@
 //
 // Layout in HBM (all device arrays owned by the index):
 //   binoff   u32 [n_blocks * dim * n_levels + 1]: bin (b, d, n_levels-1-bucket) start
-//   postings u32 (lid | w << 16) for uint8, uint2 {lid, float bits} for float32
+//   postings u32 (lid | w << 24) for uint8, uint2 {lid, float bits} for float32; each
+//            (S block, d) list padded to whole 16-byte chunks with (lid 0, weight 0)
 //   s_indptr / sp_d / sp_w: S in CSR with each row's features in pi order
 //   n_unidx  u16 [n_levels][|S|]: unindexed prefix length of s at level l
 //   ubound   u32 [n_levels][|S|]: tS of that prefix (u32 for uint8, float bits rounded up)
@@ -189,7 +190,7 @@ __global__ void k_scatter(const int64_t* __restrict__ indptr, const int32_t* __r
             uint32_t pos = atomicAdd(&cursor[bin_of(p, s, sp_d[j], bucket[j])], 1u);
             W w = sp_w[j];
             if constexpr (sizeof(W) == 1) {
-                ((uint32_t*)postings)[pos] = lid | ((uint32_t)w << 16);
+                ((uint32_t*)postings)[pos] = lid | ((uint32_t)w << 24);
             } else {
                 ((uint2*)postings)[pos] = make_uint2(lid, __float_as_uint((float)w));
             }

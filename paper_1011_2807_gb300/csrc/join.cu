@@ -3,9 +3,10 @@
 // KNN candidate set with its pruneScore kept as an exact top-k.
 //
 // One CTA owns one (query row r, group of consecutive S blocks).  Per S block b:
-//   1. threshold: theta = max(floor, score of the current k-th entry); the level l is
-//      the highest with M * L_l < theta, where M = max weight of r (l = 0 in IIB mode or
-//      while theta is 0).  Section 4.4's MinPruneScore for a one-row R block is this
+//   1. threshold: theta = the smallest score that can still enter, i.e. max(floor,
+//      score of the current k-th entry + 1 unit: that entry came from an earlier block,
+//      so a tie with it loses); the level l is the highest with M * L_l < theta, where
+//      M = max weight of r (l = 0 in IIB mode or while no k-th entry exists).  Section 4.4's MinPruneScore for a one-row R block is this
 //      row's own pruneScore, and M bounds maxWeight_d(B_r) for every d.
 //   2. scan: for each feature (d, r[d]), the prefix of list (b, d) indexed at level l
 //      is read with 128-bit loads and r[d] * w is added into a shared-memory
@@ -54,8 +55,13 @@ struct JT<uint8_t> {
     __device__ static uint32_t score_bits(int32_t v) { return (uint32_t)v; }
     __device__ static double score_of_bits(uint32_t b) { return (double)b; }
     __device__ static int32_t value_of_bits(uint32_t b) { return (int32_t)b; }
+    // posting = lid | w << 24 (lid < 2^15).  With m = r[d] << 8, the high word of
+    // posting * m is w * r[d] exactly: the low part lid * r[d] * 2^8 stays below 2^32.
+    using Mul = uint32_t;
     __device__ static int32_t post_lid(uint32_t p) { return (int32_t)(p & 0xFFFFu); }
-    __device__ static int32_t post_w(uint32_t p) { return (int32_t)(p >> 16); }
+    __device__ static int32_t post_w(uint32_t p) { return (int32_t)(p >> 24); }
+    __device__ static Mul scan_mul(int32_t rw) { return (uint32_t)rw << 8; }
+    __device__ static int32_t post_val(uint32_t p, Mul m) { return (int32_t)__umulhi(p, m); }
     __device__ static double ubound(uint32_t b) { return (double)b; }
     __device__ static u64 floor_key(float tau) {
         if (!(tau > 1.0f)) return (u64)1 << 32;
@@ -64,6 +70,13 @@ struct JT<uint8_t> {
         return (u64)(uint32_t)c << 32;
     }
     static constexpr double SLACK = 0.0;
+    // Smallest score with which an s of the current S block can still enter: the k-th
+    // key came from earlier blocks, whose ids are all smaller, so a tie with its score
+    // loses; the floor (a caller threshold or another group's k-th key) admits ties.
+    __device__ static double entry_score(u64 kth, u64 fl) {
+        const double a = kth ? (double)(uint32_t)(kth >> 32) + 1.0 : 0.0;
+        return fmax(a, (double)(uint32_t)(fl >> 32));
+    }
     // bound on the unindexed residual at a level: M * (largest integer weight sum <= L)
     __device__ static double level_bound(double M, float L) { return M * floor((double)L); }
     // smallest partial score whose upper bound (partial + lb) reaches theta
@@ -89,8 +102,11 @@ struct JT<float> {
     __device__ static uint32_t score_bits(float v) { return __float_as_uint(v); }
     __device__ static double score_of_bits(uint32_t b) { return (double)__uint_as_float(b); }
     __device__ static float value_of_bits(uint32_t b) { return __uint_as_float(b); }
+    using Mul = float;
     __device__ static int32_t post_lid(uint2 p) { return (int32_t)p.x; }
     __device__ static float post_w(uint2 p) { return __uint_as_float(p.y); }
+    __device__ static Mul scan_mul(float rw) { return rw; }
+    __device__ static float post_val(uint2 p, Mul m) { return m * __uint_as_float(p.y); }
     __device__ static double ubound(uint32_t b) { return (double)__uint_as_float(b); }
     __device__ static u64 floor_key(float tau) {
         if (!(tau > 0.0f)) return (u64)1 << 32;
@@ -98,6 +114,11 @@ struct JT<float> {
     }
     // fp32 sums may differ from the real sum by a few ulps; widen bounds a little
     static constexpr double SLACK = 1.0 / (1 << 20);
+    // as for integers, with the next float above the k-th score (scores are finite and > 0)
+    __device__ static double entry_score(u64 kth, u64 fl) {
+        const double a = kth ? (double)__uint_as_float((uint32_t)(kth >> 32) + 1u) : 0.0;
+        return fmax(a, (double)__uint_as_float((uint32_t)(fl >> 32)));
+    }
     __device__ static double level_bound(double M, float L) { return M * (double)L * (1.0 + SLACK); }
     __device__ static float cheap_min(double theta, double lb) {
         double c = (theta - lb) * (1.0 - SLACK);
@@ -160,7 +181,7 @@ __host__ __device__ inline SmemLayout smem_layout(int nb, int max_r_nnz, int rde
     L.rf_w = o; o = align16(o + (size_t)max_r_nnz * 4);
     L.lbeg = o; o = align16(o + (size_t)max_r_nnz * 8);   // two buffers (this / next S block)
     L.lend = o; o = align16(o + (size_t)max_r_nnz * 8);
-    L.ipre = o; o = align16(o + (size_t)(max_r_nnz + 1) * 4);
+    L.ipre = o; o = align16(o + (size_t)(max_r_nnz + 1) * 8);   // two buffers
     L.topk = o; o = align16(o + (size_t)KMAX * 8);
     L.sort = o; o = align16(o + (size_t)SORT_CAP * 8);
     L.cq = o;   o = align16(o + (size_t)CQ_CAP * 8);
@@ -203,7 +224,8 @@ struct CtaState {
     double lbnd[KNN_MAX_LEVELS];  // residual bound of every level for this row
     unsigned long long n_steps, n_merges, n_rounds;  // work counters (thread 0)
     int qcnt;       // entries in the completion queue
-    int pred_level; // level the next block's list ranges were prefetched for (-1: none)
+    int pred_level; // level the next block's list ranges were prepared for (-1: none)
+    int need_prepare;
     // radix select of a candidate threshold (blocks with too many candidates)
     int rs_shift, rs_need, rs_done;
     unsigned rs_prefix, rs_above, rs_key;
@@ -320,6 +342,38 @@ __device__ __forceinline__ typename JT<W>::Acc lookup_r(const int32_t* rf_d, con
 // next range of S blocks, OUT_GROUP the group's keys to p.part_keys (merged later).
 enum { OUT_FINAL = 0, OUT_CARRY = 1, OUT_GROUP = 2 };
 
+// List ranges of r's features in S block bb at level `level`, and the work items: each
+// list (starting on a 16-byte chunk) is cut into items of at most CH chunks, and
+// ipre[i] is the first item of list i (ipre[rn] = total).  One warp, lists in rounds
+// of 32 with a warp scan per round.
+template <int V, int CH>
+__device__ __forceinline__ void prepare_block_warp(const JoinParams& p, const int32_t* rf_d, int rn, int bb,
+                                                   int level, uint32_t* lbeg, uint32_t* lend, uint32_t* ipre,
+                                                   int lane) {
+    const size_t bbase = (size_t)bb * (size_t)p.dim;
+    const int off = p.n_levels - level;
+    uint32_t carry = 0;
+    for (int i0 = 0; i0 < rn; i0 += 32) {
+        const int i = i0 + lane;
+        uint32_t it = 0;
+        if (i < rn) {
+            const size_t base = (bbase + (size_t)rf_d[i]) * (size_t)p.n_levels;
+            const uint32_t a = __ldg(p.binoff + base), e = __ldg(p.binoff + base + off);
+            lbeg[i] = a;
+            lend[i] = e;
+            it = ((e - a + V - 1) / V + CH - 1) / CH;
+        }
+        uint32_t x = it;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (i < rn) ipre[i] = carry + x - it;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) ipre[rn] = carry;
+}
+
 template <class W, bool COUNT>
 __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row, const int g, const int b0,
                                          const int b1, const bool carry_in, const int out_mode,
@@ -338,7 +392,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     Acc* rf_w = (Acc*)(smem + L.rf_w);
     uint32_t* lbeg_buf = (uint32_t*)(smem + L.lbeg);
     uint32_t* lend_buf = (uint32_t*)(smem + L.lend);
-    uint32_t* ipre = (uint32_t*)(smem + L.ipre);
+    uint32_t* ipre_buf = (uint32_t*)(smem + L.ipre);
     uint32_t* cq_gid = (uint32_t*)(smem + L.cq);
     Acc* cq_v = (Acc*)(smem + L.cq + CQ_CAP * 4);
     uint8_t* rden = p.rden_dim ? (uint8_t*)(smem + L.rden) : nullptr;   // r's weights by dimension (uint8)
@@ -398,23 +452,22 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     const int chunks = nb / (T * 4);  // <= 16 by construction (mask has 64 bits)
 
     for (int b = (rn > 0 ? b0 : b1); b < b1; b++) {
-        // ---- 1. level, list ranges and work items (warp 0) ----
-        // Lane l tests level l.  This block's list ranges were requested (cp.async) during
-        // the previous block for the level that block used; they are loaded again only if
-        // the level changed.  The lists (each starting on a 16-byte chunk) are then cut
-        // into work items of at most CH chunks, and the next block's ranges requested.
+        // ---- 1. level (warp 0: lane l tests level l) ----
+        // The list ranges and work items of this block were prepared by warp 0 during the
+        // previous block's scan, for the level that block used; they are prepared here,
+        // by the whole CTA, only for a launch's first block or when the level changed.
         constexpr int V = JT<W>::PER_VEC;   // postings per 16-byte chunk
         constexpr int G = 8, U = 4, CH = G * U;
         uint32_t* lbeg = lbeg_buf + (b & 1) * p.max_r_nnz;
         uint32_t* lend = lend_buf + (b & 1) * p.max_r_nnz;
+        uint32_t* ipre = ipre_buf + (b & 1) * (p.max_r_nnz + 1);
         if (warp == 0) {
             u64 fl = st.floor;
             if (p.floor_keys) {
                 u64 shared = *(volatile u64*)(p.floor_keys + row);
                 if (shared > fl) fl = shared;
             }
-            const u64 eff = st.kth > fl ? st.kth : fl;
-            const double theta = JT<W>::score_of_bits((uint32_t)(eff >> 32));
+            const double theta = JT<W>::entry_score(st.kth, fl);
             bool ok = false;
             if (p.iiib && lane >= 1 && lane < p.n_levels) {
                 const double lb = st.lbnd[lane];
@@ -422,72 +475,49 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
             const int level = m ? 31 - __clz(m) : 0;
-            const int pred = st.pred_level;
-            asm volatile("cp.async.wait_all;" ::: "memory");
-            __syncwarp();
-            if (pred != level) {
-                const size_t bbase = (size_t)b * (size_t)p.dim;
-                for (int i = lane; i < rn; i += 32) {
-                    size_t base = (bbase + (size_t)rf_d[i]) * (size_t)p.n_levels;
-                    lbeg[i] = p.binoff[base];
-                    lend[i] = p.binoff[base + (size_t)(p.n_levels - level)];
-                }
-            }
-            __syncwarp();
-            // work items: exclusive prefix of ceil(chunks / CH) over the lists
-            const int per = (rn + 31) / 32;
-            const int a0 = min(rn, lane * per), a1 = min(rn, a0 + per);
-            uint32_t sum = 0;
-            for (int i = a0; i < a1; i++) {
-                const uint32_t nch = (lend[i] - lbeg[i] + V - 1) / V;
-                const uint32_t it = (nch + CH - 1) / CH;
-                ipre[i] = it;
-                sum += it;
-            }
-            uint32_t x = sum;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            uint32_t run = x - sum;
-            for (int i = a0; i < a1; i++) {
-                const uint32_t c = ipre[i];
-                ipre[i] = run;
-                run += c;
-            }
-            if (lane == 31) ipre[rn] = x;
-            if (b + 1 < b1) {   // next block's ranges, assuming the level stays
-                uint32_t* nbeg = lbeg_buf + ((b + 1) & 1) * p.max_r_nnz;
-                uint32_t* nend = lend_buf + ((b + 1) & 1) * p.max_r_nnz;
-                const size_t nbase = (size_t)(b + 1) * (size_t)p.dim;
-                for (int i = lane; i < rn; i += 32) {
-                    size_t base = (nbase + (size_t)rf_d[i]) * (size_t)p.n_levels;
-                    cp_async4(nbeg + i, p.binoff + base);
-                    cp_async4(nend + i, p.binoff + base + (size_t)(p.n_levels - level));
-                }
-                cp_async_commit();
-            }
             if (lane == 0) {
                 st.floor = fl;
                 st.theta = theta;
                 st.level = level;
+                st.need_prepare = st.pred_level != level;
                 st.pending = 0;
                 st.n_steps++;
                 st.lb = st.lbnd[level];
-                st.pred_level = b + 1 < b1 ? level : -1;
                 JT<W>::set_cmin(st, JT<W>::cheap_min(theta, st.lb));
             }
         }
         __syncthreads();
         const int level = st.level;
+        if (st.need_prepare) {
+            const size_t bbase = (size_t)b * (size_t)p.dim;
+            for (int i = tid; i < rn; i += T) {
+                const size_t base = (bbase + (size_t)rf_d[i]) * (size_t)p.n_levels;
+                const uint32_t a = __ldg(p.binoff + base), e = __ldg(p.binoff + base + (p.n_levels - level));
+                lbeg[i] = a;
+                lend[i] = e;
+                ipre[i] = ((e - a + V - 1) / V + CH - 1) / CH;
+            }
+            __syncthreads();
+            cta_exclusive_scan(ipre, rn, (uint32_t*)red_u);
+        }
         // ---- 2. scan: acc[lid] += r[d] * w over the indexed prefixes ----
         // Each 8-lane sub-warp takes an equal contiguous range of work items, so every
         // sub-warp runs the same number of iterations; per item each lane loads U chunks
         // (one 128-byte line per sub-warp per load) before adding.  Only the last chunk
         // of a prefix can be partial (lists start on chunk boundaries).
-        {
+        // With 4 or more warps, warp 0 instead prepares the next block (for this level)
+        // while the others scan, so that work leaves the critical path.
+        const bool producer = nwarps >= 4;
+        if (producer && warp == 0) {
+            if (b + 1 < b1)
+                prepare_block_warp<V, CH>(p, rf_d, rn, b + 1, level, lbeg_buf + ((b + 1) & 1) * p.max_r_nnz,
+                                          lend_buf + ((b + 1) & 1) * p.max_r_nnz,
+                                          ipre_buf + ((b + 1) & 1) * (p.max_r_nnz + 1), lane);
+            if (lane == 0) st.pred_level = b + 1 < b1 ? level : -1;
+        } else {
             const Post* post = (const Post*)p.postings;
-            const int nsub = T / G, sub = tid / G, sl = tid % G;
+            const int t0 = producer ? 32 : 0;
+            const int nsub = (T - t0) / G, sub = (tid - t0) / G, sl = tid % G;
             const uint32_t total = ipre[rn];
             const uint32_t per = (total + nsub - 1) / nsub;
             const uint32_t I0 = min(total, (uint32_t)sub * per), I1 = min(total, I0 + per);
@@ -501,30 +531,31 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                 }
                 li = lo;
             }
+            using Mul = typename JT<W>::Mul;
             for (uint32_t I = I0; I < I1; I++) {
                 while (ipre[li + 1] <= I) li++;
                 const uint32_t en = lend[li];
-                const Acc rw = rf_w[li];
-                const uint32_t p0 = lbeg[li] + (I - ipre[li]) * (CH * V);   // first posting of the item
-                const Post* base = post + p0;
+                const Mul m = JT<W>::scan_mul(rf_w[li]);
+                const uint32_t p0 = lbeg[li] + (I - ipre[li]) * (CH * V) + (uint32_t)sl * V;   // this lane's first posting
+                const uint4* src = (const uint4*)(post + p0);
                 uint4 v[U];
 #pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const uint32_t q = p0 + (uint32_t)(sl + G * u) * V;
-                    if (q < en) v[u] = *(const uint4*)(base + (sl + G * u) * V);
-                }
+                for (int u = 0; u < U; u++)
+                    if (p0 + (uint32_t)(G * u * V) < en) v[u] = src[G * u];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    const uint32_t q = p0 + (uint32_t)(sl + G * u) * V;
+                    const uint32_t q = p0 + (uint32_t)(G * u * V);
                     if (q < en) {
+                        // postings of the chunk past the prefix end (level > 0) belong to the
+                        // same list: they are added with weight 0 rather than branched around
                         const Post* e = (const Post*)&v[u];
-                        const uint32_t nv = min((uint32_t)V, en - q);
+                        const uint32_t nv = en - q;
 #pragma unroll
                         for (int j = 0; j < V; j++) {
-                            if (j < (int)nv) {
-                                red_add_shared(acc_s + 4u * (uint32_t)JT<W>::post_lid(e[j]), rw * JT<W>::post_w(e[j]));
-                                if (COUNT) n_post += JT<W>::post_w(e[j]) != (Acc)0;   // padding has weight 0
-                            }
+                            const bool in = j == 0 || (uint32_t)j < nv;
+                            red_add_shared(acc_s + 4u * (uint32_t)JT<W>::post_lid(e[j]),
+                                           JT<W>::post_val(e[j], in ? m : (Mul)0));
+                            if (COUNT) n_post += in && JT<W>::post_w(e[j]) != 0;   // padding has weight 0
                         }
                     }
                 }
