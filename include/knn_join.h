@@ -156,7 +156,7 @@ typedef struct {
                                    synchronises `stream` before returning                */
     int32_t skip_validation;    /* 1: trust R (sorted, in range, w > 0)                   */
     float level_margin;         /* Section 4.4 cut per S block: the highest level l with
-                                   M * L_l <= level_margin * theta (0 = 0.25).  Lower values
+                                   M * L_l <= level_margin * theta (0 = 0.4).  Lower values
                                    scan more postings and complete fewer candidates.     */
     int64_t* stats;             /* device int64[KNN_STATS_LEN] or NULL: work counters,
                                    added to (see KNN_STAT_*)                              */
@@ -209,7 +209,7 @@ typedef struct {
     int32_t threads;            /* threads per CTA for every job, power of two; 0 = 512.
                                    Every job's S block must lie in [4*threads, 64*threads]. */
     int32_t blocks_per_group;   /* S blocks per work item; 0 = 16                            */
-    float level_margin;         /* as in knn_join_opts (0 = 0.25)                            */
+    float level_margin;         /* as in knn_join_opts (0 = 0.4)                             */
     int32_t use_graph;          /* knn_batch_create: capture the launch into a CUDA graph   */
     int32_t skip_validation;    /* 1: trust every R                                          */
     int64_t* stats;             /* device int64[KNN_STATS_LEN] or NULL (all jobs together)   */
@@ -290,15 +290,27 @@ knn_status knn_threshold_model_train(knn_model* model, const knn_csr* Q, const f
 knn_status knn_threshold_model_predict(const knn_model* model, const knn_csr* R, float* out_tau,
                                        void* stream);
 
-/* Save / load: all parameters and optimiser state as one host buffer.  With
- * host_buf = NULL, get_params only reports the size in *needed.                  */
+/* Calibrates the multiplier applied to the predictions: on held-out queries Q with
+ * their exact k-th best scores (device float[Q.n_rows], 0 = no k-th score), picks the
+ * largest tau_scale such that at most a fraction miss_rate of Q would start above its
+ * k-th score (those rows need knn_join_learned's fallback; rows without a k-th score
+ * always do).  The value (rank floor(miss_rate * n) of kth / prediction, less a
+ * relative 1e-6 so that rounding cannot lift a row at that rank over) is kept in
+ * the model, saved with its parameters, used by knn_join_learned when its tau_scale
+ * is 0, and written to *out_scale (host, may be NULL).  Synchronises `stream`.      */
+knn_status knn_threshold_model_calibrate(knn_model* model, const knn_csr* Q, const float* kth_scores,
+                                         float miss_rate, float* out_scale, void* stream);
+
+/* Save / load: all parameters, optimiser state and the calibrated multiplier as one
+ * host buffer.  With host_buf = NULL, get_params only reports the size in *needed.  */
 knn_status knn_threshold_model_get_params(const knn_model* model, void* host_buf, size_t bytes,
                                           size_t* needed);
 knn_status knn_threshold_model_set_params(knn_model* model, const void* host_buf, size_t bytes);
 
 typedef struct {
     knn_join_opts join;   /* options of both passes (init_threshold, n_found are set here) */
-    float tau_scale;      /* multiplies the predictions (0 = 1)                          */
+    float tau_scale;      /* multiplies the predictions (0 = the model's calibrated
+                             multiplier, 1 if it was never calibrated)                  */
     const float* tau;     /* device float[n_rows]: start thresholds to use instead of the
                              model's (the model may then be NULL)                       */
 } knn_learned_opts;

@@ -2,7 +2,8 @@
 
 The S block size (fixed when an index is built), the threads per CTA and the number of
 S blocks per launch (or per batched work item) are picked per class of join, by timing
-candidate configurations on a small sample of the join itself.  A class is keyed by
+candidate configurations on a small sample of the join itself; the Section 4.4 level
+margin is then timed on the winning configuration.  A class is keyed by
 dtype and the rounded base-2 logarithms of |S|, |R|, the mean query length and k, so
 every join of similar shape reuses one measurement.  Results are cached in a JSON file
 (``$KNN_TUNE_CACHE``, else ``~/.cache/knnjoin_gb300/tune.json``).
@@ -21,7 +22,8 @@ import numpy as np
 
 _lock = threading.Lock()
 
-DEFAULT = {"block_size": 16384, "threads": 512, "blocks_per_launch": 8}
+DEFAULT = {"block_size": 16384, "threads": 512, "blocks_per_launch": 8, "level_margin": 0.4}
+MARGINS = (0.25, 0.4, 0.55)
 
 
 def cache_path() -> str:
@@ -67,7 +69,9 @@ def heuristic(n_s: int) -> dict:
 def lookup(n_s: int, n_r: int, mean_nnz: float, k: int, dtype: str = "u8") -> dict:
     with _lock:
         d = _load()
-    return dict(d.get(class_key(n_s, n_r, mean_nnz, k, dtype), heuristic(n_s)))
+    got = dict(d.get(class_key(n_s, n_r, mean_nnz, k, dtype), heuristic(n_s)))
+    got.setdefault("level_margin", DEFAULT["level_margin"])
+    return got
 
 
 def candidates(n_s: int, threads: int | None = None):
@@ -86,7 +90,7 @@ def candidates(n_s: int, threads: int | None = None):
 
 
 def tune(S, R_sample, k: int, *, threads: int | None = None, reps: int = 2, store: bool = True,
-         max_trials: int = 24) -> dict:
+         max_trials: int = 24, tune_margin: bool = True) -> dict:
     """Times the candidates on (S, R_sample) and returns (and caches) the fastest."""
     import torch
     from . import binding
@@ -105,7 +109,8 @@ def tune(S, R_sample, k: int, *, threads: int | None = None, reps: int = 2, stor
         idx = binding.knn_join_build_index(S, block_size=bs)
         try:
             for c in cs:
-                kw = dict(threads=c["threads"], blocks_per_launch=c["blocks_per_launch"], skip_validation=True)
+                kw = dict(threads=c["threads"], blocks_per_launch=c["blocks_per_launch"],
+                          level_margin=DEFAULT["level_margin"], skip_validation=True)
                 binding.knn_join(idx, Rd, k, **kw)   # warm-up (and validation of R on first use)
                 torch.cuda.synchronize()
                 ms = float("inf")
@@ -122,8 +127,32 @@ def tune(S, R_sample, k: int, *, threads: int | None = None, reps: int = 2, stor
                     best, best_ms = dict(c), ms
         finally:
             idx.close()
+    if best is not None and tune_margin:
+        idx = binding.knn_join_build_index(S, block_size=best["block_size"])
+        try:
+            for mg in MARGINS:
+                kw = dict(threads=best["threads"], blocks_per_launch=best["blocks_per_launch"], level_margin=mg,
+                          skip_validation=True)
+                binding.knn_join(idx, Rd, k, **kw)
+                torch.cuda.synchronize()
+                ms = float("inf")
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    binding.knn_join(idx, Rd, k, **kw)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms = min(ms, e0.elapsed_time(e1))
+                trials.append(dict(best, level_margin=mg, ms=ms))
+                if ms < best_ms:
+                    best_ms = ms
+                    best["level_margin"] = mg
+        finally:
+            idx.close()
     if best is None:
         best = heuristic(S.n_rows)
+    best.setdefault("level_margin", DEFAULT["level_margin"])
     best["ms"] = best_ms
     best["trials"] = len(trials)
     if store:

@@ -342,6 +342,8 @@ def _model_lib():
         L.knn_threshold_model_train.argtypes = [ctypes.c_void_p, P(_Csr), ctypes.c_void_p, P(_TrainOpts),
                                                 P(ctypes.c_float), ctypes.c_void_p]
         L.knn_threshold_model_predict.argtypes = [ctypes.c_void_p, P(_Csr), ctypes.c_void_p, ctypes.c_void_p]
+        L.knn_threshold_model_calibrate.argtypes = [ctypes.c_void_p, P(_Csr), ctypes.c_void_p, ctypes.c_float,
+                                                    P(ctypes.c_float), ctypes.c_void_p]
         L.knn_threshold_model_get_params.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                                      P(ctypes.c_size_t)]
         L.knn_threshold_model_set_params.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
@@ -388,6 +390,17 @@ class ThresholdModel:
         _check(L, L.knn_threshold_model_train(self.handle, ctypes.byref(c), kth.data_ptr(), ctypes.byref(o),
                                               ctypes.byref(loss), _stream_ptr(stream)))
         return float(loss.value)
+
+    def calibrate(self, Q, kth_scores: torch.Tensor, miss_rate: float, stream=None) -> float:
+        """Sets (and returns) the prediction multiplier for a target fallback rate."""
+        L = _model_lib()
+        keep = []
+        c = _csr(Q, keep)
+        kth = kth_scores.contiguous().float()
+        out = ctypes.c_float(0.0)
+        _check(L, L.knn_threshold_model_calibrate(self.handle, ctypes.byref(c), kth.data_ptr(), float(miss_rate),
+                                                  ctypes.byref(out), _stream_ptr(stream)))
+        return float(out.value)
 
     def predict(self, R, stream=None) -> torch.Tensor:
         L = _model_lib()

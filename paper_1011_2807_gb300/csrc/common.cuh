@@ -144,6 +144,8 @@ inline int launch_blocks(int64_t work, int per_block, int64_t cap = (1LL << 31) 
 // Predicted k-th scores (device float[n_rows]) of a device CSR with the model.
 knn_status model_predict_tau(const knn_model* md, const DevCSR& r, float tau_scale, float* tau, cudaStream_t s,
                              Buffers& tmp);
+// The model's calibrated prediction multiplier (1 until knn_threshold_model_calibrate).
+float model_tau_scale(const knn_model* md);
 
 // Exclusive scan of u32 counts (n elements) into out[0..n], out[n] = total.
 // The total must stay below 2^32 (checked by the caller).  Works in place.

@@ -224,6 +224,8 @@ struct CtaState {
     double lbnd[KNN_MAX_LEVELS];  // residual bound of every level for this row
     unsigned long long n_steps, n_merges, n_rounds;  // work counters (thread 0)
     int qcnt;       // entries in the completion queue
+    int dq_n;       // candidates deferred to warp 0 (in the completion queue's arrays)
+    int dq_level;   // level of the block they came from
     int pred_level; // level the next block's list ranges were prepared for (-1: none)
     int need_prepare;
     // radix select of a candidate threshold (blocks with too many candidates)
@@ -432,6 +434,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         st.floor = p.init_thr ? JT<W>::floor_key(p.init_thr[row]) : ((u64)1 << 32);
         st.n_steps = st.n_merges = st.n_rounds = 0;
         st.qcnt = 0;
+        st.dq_n = 0;
         st.pred_level = -1;
         for (int l = 0; l < p.n_levels; l++) st.lbnd[l] = l ? JT<W>::level_bound(m, p.levels[l]) : 0.0;
     }
@@ -450,6 +453,77 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     uint32_t n_cand = 0, n_comp = 0, n_push = 0, n_resf = 0;   // this thread's counters
     unsigned long long n_post = 0;                              // postings (sub-warp leaders)
     const int chunks = nb / (T * 4);  // <= 16 by construction (mask has 64 bits)
+
+    // Warp 0 completes and merges the candidates a block deferred (few of them): one lane
+    // per candidate, keys inserted into the sorted top-k one at a time.  Runs during the
+    // next block's scan, or after the last block.
+    auto drain = [&]() {
+        const int n = st.dq_n;
+        if (n == 0) return;
+        const int lvl = st.dq_level;
+        const double Mr = st.M;
+        const u64 fl = st.floor;
+        u64 kth = st.kth;
+        int sz = st.size;
+        bool merged = false;
+        for (int e0 = 0; e0 < n; e0 += 32) {
+            const int e = e0 + lane;
+            u64 key = 0ull;
+            bool ins = false;
+            if (e < n) {
+                const uint32_t gid = cq_gid[e];
+                Acc v = cq_v[e];
+                bool ok = true;
+                if (lvl > 0) {
+                    const double th = JT<W>::score_of_bits((uint32_t)((kth > fl ? kth : fl) >> 32));
+                    ok = JT<W>::exact_ok(v, Mr, p.ubound[(int64_t)lvl * p.n_s + gid], th);
+                    if (ok) {   // Algorithm 4's dot over the unindexed features
+                        const int64_t j0 = p.s_indptr[gid];
+                        const int m = p.n_unidx[(int64_t)lvl * p.n_s + gid];
+                        Acc res = (Acc)0;
+                        for (int q = 0; q < m; q++) {
+                            const int32_t d = p.sp_d[j0 + q];
+                            const Acc w = (Acc)((const W*)p.sp_w)[j0 + q];
+                            res += (rden ? (Acc)rden[d] : lookup_r<W>(rf_d, rf_w, rn, d)) * w;
+                        }
+                        v += res;
+                        n_comp++;
+                        n_resf += m;
+                    }
+                }
+                if (ok) {
+                    key = make_key(JT<W>::score_bits(v), gid);
+                    ins = key >= fl && key > kth;
+                }
+            }
+            for (unsigned bal = __ballot_sync(0xffffffffu, ins); bal; bal &= bal - 1) {
+                const u64 kk = __shfl_sync(0xffffffffu, key, __ffs(bal) - 1);
+                if (sz == p.k && kk <= kth) continue;
+                int c = 0;
+                for (int i = lane; i < sz; i += 32) c += topk[i] > kk;
+                const int pos = __reduce_add_sync(0xffffffffu, c);
+                const int nsz = min(sz + 1, p.k);
+                const int i0 = pos + lane, i1 = pos + lane + 32;   // k <= 64
+                const u64 t0 = i0 < nsz - 1 ? topk[i0] : 0ull, t1 = i1 < nsz - 1 ? topk[i1] : 0ull;
+                __syncwarp();
+                if (i0 < nsz - 1) topk[i0 + 1] = t0;
+                if (i1 < nsz - 1) topk[i1 + 1] = t1;
+                if (lane == 0) topk[pos] = kk;
+                __syncwarp();
+                sz = nsz;
+                kth = sz == p.k ? topk[p.k - 1] : 0ull;
+                if (lane == 0) n_push++;
+                merged = true;
+            }
+        }
+        if (lane == 0) {
+            st.size = sz;
+            st.kth = kth;
+            st.dq_n = 0;
+            if (merged) st.n_merges++;
+        }
+        __syncwarp();
+    };
 
     for (int b = (rn > 0 ? b0 : b1); b < b1; b++) {
         // ---- 1. level (warp 0: lane l tests level l) ----
@@ -509,6 +583,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         // while the others scan, so that work leaves the critical path.
         const bool producer = nwarps >= 4;
         if (producer && warp == 0) {
+            drain();   // the previous block's deferred candidates
             if (b + 1 < b1)
                 prepare_block_warp<V, CH>(p, rf_d, rn, b + 1, level, lbeg_buf + ((b + 1) & 1) * p.max_r_nnz,
                                           lend_buf + ((b + 1) & 1) * p.max_r_nnz,
@@ -594,7 +669,21 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
         if (lane == 0 && wsum) atomicAdd(&st.pending, wsum);
         __syncthreads();
-        if (st.pending > 0) {   // most blocks, once the threshold has settled, have none
+        const int pend = st.pending;   // most blocks, once the threshold has settled, have none
+        if (pend > 0 && producer && pend <= CQ_CAP) {
+            // Few candidates: queue them for warp 0, which completes and merges them during
+            // the next block's scan.  That block's threshold is then one block stale, which
+            // only loosens its pruning.
+            for (; mask; mask &= mask - 1) {
+                const int bit = __ffsll(mask) - 1;
+                const int lid = (bit >> 2) * T * 4 + tid * 4 + (bit & 3);
+                const int slot = atomicAdd(&st.dq_n, 1);
+                cq_gid[slot] = (uint32_t)(gbase + lid);
+                cq_v[slot] = acc[lid];
+                acc[lid] = (Acc)0;
+            }
+            if (tid == 0) st.dq_level = level;
+        } else if (pend > 0) {
         if (st.pending > PUSH_CAP) {
             // Too many candidates for one merge (typically the first block, where the
             // threshold is still 0).  Radix-select, on the candidates' partial scores,
@@ -758,6 +847,10 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         }   // st.pending > 0
         // publish this group's k-th key as a floor for the other groups of the row
         if (tid == 0 && p.floor_keys && st.size == p.k) atomicMax(p.floor_keys + row, st.kth);
+        __syncthreads();
+    }
+    if (nwarps >= 4) {   // the last block's deferred candidates
+        if (warp == 0) drain();
         __syncthreads();
     }
 
@@ -1021,7 +1114,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     p.n_found = o.n_found;
     p.touched = (unsigned long long*)o.postings_scanned;
     p.stats = (unsigned long long*)o.stats;
-    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 0.25f;
+    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 0.4f;
     if (!(p.level_margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     if (groups > 1) {
         KNN_TRY(tmp.get(&p.part_keys, (size_t)r.n_rows * groups * k));
@@ -1195,7 +1288,7 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     p.n_found = o.n_found;
     p.touched = (unsigned long long*)o.postings_scanned;
     p.stats = (unsigned long long*)o.stats;
-    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 0.25f;
+    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 0.4f;
     if (!(p.level_margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     p.carry = (u64*)((unsigned char*)scratch + NOALLOC_HEADER);
 
@@ -1280,7 +1373,7 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
     knn_batch_opts o = {};
     if (opts) o = *opts;
     if (o.mode != KNN_MODE_IIIB && o.mode != KNN_MODE_IIB) return fail(KNN_EINVAL, "unknown mode");
-    const float margin = o.level_margin > 0.0f ? o.level_margin : 0.25f;
+    const float margin = o.level_margin > 0.0f ? o.level_margin : 0.4f;
     if (!(margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     int dev = 0, smem_optin = 0, n_sm = 0;
     KNN_CUDA_TRY(cudaGetDevice(&dev));

@@ -293,6 +293,13 @@ __global__ void k_log_labels(const float* __restrict__ kth, int64_t n, float* __
 }
 
 // tau = exp(y) (the predicted k-th score), optional scale
+// kth / tau per row (+inf where the row has no k-th score: it falls back whatever tau is)
+__global__ void k_kth_ratio(const float* __restrict__ kth, const float* __restrict__ tau, int64_t n,
+                            float* __restrict__ ratio) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) ratio[i] = kth[i] > 0.0f && tau[i] > 0.0f ? kth[i] / tau[i] : __int_as_float(0x7f800000);
+}
+
 __global__ void k_exp_tau(const float* __restrict__ y, int64_t n, float scale, float* __restrict__ tau) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) tau[i] = expf(y[i]) * scale;
@@ -316,6 +323,7 @@ struct knn_model {
     float* grad = nullptr;
     __nv_bfloat16* wb = nullptr;
     int64_t n_params = 0;
+    float tau_scale = 1.0f;   // calibrated multiplier of the predictions (1 until calibrated)
 };
 
 namespace knn {
@@ -404,6 +412,8 @@ static knn_status sketch(const DevCSR& r, uint32_t seed, __nv_bfloat16* X, cudaS
     count_launch();
     return KNN_OK;
 }
+
+float model_tau_scale(const knn_model* md) { return md->tau_scale; }
 
 // predicted k-th scores for every row of r (device float[n_rows]) in chunks
 knn_status model_predict_tau(const knn_model* md, const DevCSR& r, float tau_scale, float* tau, cudaStream_t s,
@@ -582,10 +592,44 @@ extern "C" knn_status knn_threshold_model_predict(const knn_model* md, const knn
     return KNN_OK;
 }
 
+extern "C" knn_status knn_threshold_model_calibrate(knn_model* md, const knn_csr* Q, const float* kth_scores,
+                                                   float miss_rate, float* out_scale, void* stream_) {
+    if (!md || !Q || !kth_scores) return fail(KNN_EINVAL, "NULL argument");
+    if (!(miss_rate >= 0.0f && miss_rate < 1.0f)) return fail(KNN_EINVAL, "miss_rate must be in [0, 1)");
+    cudaStream_t s = (cudaStream_t)stream_;
+    Buffers tmp(s);
+    DevCSR q;
+    KNN_TRY(prepare_csr(Q, s, tmp, true, false, &q));
+    if (q.n_rows == 0) return fail(KNN_EINVAL, "no calibration queries");
+    float* tau = nullptr;
+    float* ratio = nullptr;
+    KNN_TRY(tmp.get(&tau, (size_t)q.n_rows));
+    KNN_TRY(tmp.get(&ratio, (size_t)q.n_rows));
+    KNN_TRY(model_predict_tau(md, q, 1.0f, tau, s, tmp));
+    k_kth_ratio<<<launch_blocks(q.n_rows, 256), 256, 0, s>>>(kth_scores, tau, q.n_rows, ratio);
+    KNN_CUDA_TRY(cudaGetLastError());
+    count_launch();
+    std::vector<float> h((size_t)q.n_rows);
+    KNN_CUDA_TRY(cudaMemcpyAsync(h.data(), ratio, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, s));
+    KNN_CUDA_TRY(cudaStreamSynchronize(s));
+    // A row falls back iff scale * tau > kth, i.e. scale > kth / tau.  The value at rank
+    // floor(miss_rate * n) leaves at most that many rows of Q below it; it is stepped down
+    // by a relative 1e-6 so that the rounding of scale * tau cannot lift the row at that
+    // rank (or rows tied with it) above their k-th score.
+    const size_t idx = std::min(h.size() - 1, (size_t)std::floor((double)miss_rate * (double)h.size()));
+    std::nth_element(h.begin(), h.begin() + (ptrdiff_t)idx, h.end());
+    float scale = (float)((double)h[idx] * (1.0 - 1e-6));
+    if (!(scale < 3.0e38f)) return fail(KNN_EINVAL, "too few calibration rows with a k-th score");
+    if (!(scale > 0.0f)) scale = 1.0e-30f;
+    md->tau_scale = scale;
+    if (out_scale) *out_scale = scale;
+    return KNN_OK;
+}
+
 extern "C" knn_status knn_threshold_model_get_params(const knn_model* md, void* host_buf, size_t bytes,
                                                     size_t* needed) {
     if (!md) return fail(KNN_EINVAL, "model is NULL");
-    const size_t need = sizeof(uint32_t) * 2 + sizeof(int64_t) + sizeof(float) * 3 * N_PARAMS;
+    const size_t need = sizeof(uint32_t) * 2 + sizeof(int64_t) + sizeof(float) * (3 * N_PARAMS + 1);
     if (needed) *needed = need;
     if (!host_buf) return KNN_OK;
     if (bytes < need) return fail(KNN_EINVAL, "buffer of %zu bytes, %zu needed", bytes, need);
@@ -600,13 +644,14 @@ extern "C" knn_status knn_threshold_model_get_params(const knn_model* md, void* 
                                  md->stream));
     KNN_CUDA_TRY(cudaMemcpyAsync(p + 2 * sizeof(float) * N_PARAMS, md->v, sizeof(float) * N_PARAMS,
                                  cudaMemcpyDeviceToHost, md->stream));
+    memcpy(p + 3 * sizeof(float) * N_PARAMS, &md->tau_scale, sizeof(float));
     KNN_CUDA_TRY(cudaStreamSynchronize(md->stream));
     return KNN_OK;
 }
 
 extern "C" knn_status knn_threshold_model_set_params(knn_model* md, const void* host_buf, size_t bytes) {
     if (!md || !host_buf) return fail(KNN_EINVAL, "NULL argument");
-    const size_t need = sizeof(uint32_t) * 2 + sizeof(int64_t) + sizeof(float) * 3 * N_PARAMS;
+    const size_t need = sizeof(uint32_t) * 2 + sizeof(int64_t) + sizeof(float) * (3 * N_PARAMS + 1);
     if (bytes < need) return fail(KNN_EINVAL, "buffer of %zu bytes, %zu needed", bytes, need);
     const unsigned char* p = (const unsigned char*)host_buf;
     uint32_t hdr[2];
@@ -621,6 +666,10 @@ extern "C" knn_status knn_threshold_model_set_params(knn_model* md, const void* 
                                  md->stream));
     KNN_CUDA_TRY(cudaMemcpyAsync(md->v, p + 2 * sizeof(float) * N_PARAMS, sizeof(float) * N_PARAMS,
                                  cudaMemcpyHostToDevice, md->stream));
+    float scale = 1.0f;
+    memcpy(&scale, p + 3 * sizeof(float) * N_PARAMS, sizeof(float));
+    if (!(scale > 0.0f) || !(scale < 3.0e38f)) return fail(KNN_EINVAL, "stored tau scale %g is not a positive number", scale);
+    md->tau_scale = scale;
     k_to_bf16<<<launch_blocks(N_PARAMS, 256), 256, 0, md->stream>>>(md->w, md->wb, N_PARAMS);
     KNN_CUDA_TRY(cudaGetLastError());
     count_launch();

@@ -29,6 +29,7 @@ def test_heuristic_and_cache_roundtrip(tmp_path, monkeypatch):
     autotune._store({key: {"block_size": 8192, "threads": 256, "blocks_per_launch": 4}})
     got = autotune.lookup(50000, 300, 120, 10, "u8")
     assert got["block_size"] == 8192 and got["threads"] == 256
+    assert got["level_margin"] == autotune.DEFAULT["level_margin"]   # entries cached without a margin
     assert json.load(open(tmp_path / "tune.json"))[key]["blocks_per_launch"] == 4
     # an unseen class falls back to the heuristic
     assert autotune.lookup(12, 1, 1, 1, "f32")["block_size"] == 2048

@@ -250,3 +250,46 @@ def test_good_thresholds_scan_fewer_postings(knn, trained):
     assert st["fallback_rows"] == 0
     assert torch.equal(pids, lids) and torch.equal(psc, lsc)
     assert int(c_l.item()) < int(c_plain.item())
+
+
+def test_calibrate_picks_the_ratio_quantile(knn, trained):
+    m = knn.ThresholdModel(seed=7)
+    m.set_params(trained["model"].get_params())
+    V = synth.spectrum_u8(800, 371, role="R")
+    _, vsc = knn.knn_join(trained["idx"], knn.DeviceCSR.from_host(V), 5)
+    kth = vsc[:, 4].float().contiguous()
+    scale = m.calibrate(V, kth, 0.05)
+    pred = m.predict(V).cpu().numpy()
+    kk = kth.cpu().numpy()
+    ratio = np.full(len(kk), np.inf, dtype=np.float32)
+    ok = (kk > 0) & (pred > 0)
+    ratio[ok] = kk[ok] / pred[ok]
+    expect = np.sort(ratio)[int(np.floor(0.05 * len(ratio)))]
+    assert abs(scale - expect) <= 1e-5 * expect, (scale, expect)
+    assert (pred * scale > kk).mean() <= 0.05 + 1e-9
+    # the multiplier travels with the parameters and is the learned join's default
+    m2 = knn.ThresholdModel(seed=8)
+    m2.set_params(m.get_params())
+    W = synth.spectrum_u8(300, 372, role="R")
+    Wd = knn.DeviceCSR.from_host(W)
+    a = knn.knn_join_learned(trained["idx"], m2, Wd, 5)
+    b = knn.knn_join_learned(trained["idx"], m, Wd, 5, tau_scale=scale)
+    assert a[2]["fallback_rows"] == b[2]["fallback_rows"]
+    pids, psc = knn.knn_join(trained["idx"], Wd, 5)
+    import torch
+    assert torch.equal(a[0], pids) and torch.equal(a[1], psc)
+    m.close()
+    m2.close()
+
+
+def test_calibrated_fallback_rate_on_fresh_queries(knn, trained):
+    m = knn.ThresholdModel(seed=9)
+    m.set_params(trained["model"].get_params())
+    V = synth.spectrum_u8(1500, 381, role="R")
+    _, vsc = knn.knn_join(trained["idx"], knn.DeviceCSR.from_host(V), 5)
+    m.calibrate(V, vsc[:, 4].float().contiguous(), 0.02)
+    E = synth.spectrum_u8(1500, 382, role="R")
+    _, _, st = knn.knn_join_learned(trained["idx"], m, knn.DeviceCSR.from_host(E), 5)
+    # a 2 % target on 1,500 fresh rows: far from the 100 % an uncalibrated over-prediction gives
+    assert st["fallback_rows"] <= 0.08 * E.n_rows, st
+    m.close()
