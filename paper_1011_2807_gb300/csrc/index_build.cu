@@ -198,6 +198,56 @@ __global__ void k_scatter(const int64_t* __restrict__ indptr, const int32_t* __r
     }
 }
 
+// Orders the postings of every bin inside each work item of its list (32 chunks, the
+// unit the join's scan hands to an 8-lane group) so that postings in the same slot j of
+// the item's chunks fall into different shared-memory banks (local id mod 32) wherever
+// the bin's contents allow: the 8 lanes of a group add slot j of 8 consecutive chunks
+// with one instruction.  Only the order inside a bin changes, so every level's prefix
+// keeps the same postings.  One thread per (S block, d) list.
+template <class Post, int V>
+__device__ __forceinline__ uint32_t post_bank(Post e);
+template <>
+__device__ __forceinline__ uint32_t post_bank<uint32_t, 4>(uint32_t e) { return e & 31u; }
+template <>
+__device__ __forceinline__ uint32_t post_bank<uint2, 2>(uint2 e) { return e.x & 31u; }
+
+template <class Post, int V>
+__global__ void k_arrange(const uint32_t* __restrict__ binoff, int64_t n_lists, int32_t n_levels,
+                          Post* __restrict__ post) {
+    constexpr int ITEM = 32 * V;   // postings of one work item
+    const int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (li >= n_lists) return;
+    const uint32_t* bo = binoff + li * n_levels;
+    const uint32_t L0 = bo[0], L1 = bo[n_levels];   // the next list's start
+    Post buf[ITEM];
+    for (uint32_t a = L0; a < L1; a += ITEM) {
+        const uint32_t b = min(L1, a + (uint32_t)ITEM);
+        uint32_t used[V];
+#pragma unroll
+        for (int j = 0; j < V; j++) used[j] = 0u;
+        for (int t = 0; t < n_levels; t++) {
+            const uint32_t x = max(bo[t], a), y = min(bo[t + 1], b);
+            if (x >= y) continue;
+            int rem = (int)(y - x);
+            for (int i = 0; i < rem; i++) buf[i] = post[x + i];
+            for (uint32_t q = x; q < y; q++) {
+                uint32_t& u = used[q & (V - 1)];
+                int pick = 0;
+                for (int c = 0; c < rem; c++)
+                    if (!((u >> post_bank<Post, V>(buf[c])) & 1u)) {
+                        pick = c;
+                        break;
+                    }
+                const Post e = buf[pick];
+                buf[pick] = buf[rem - 1];
+                rem--;
+                post[q] = e;
+                u |= 1u << post_bank<Post, V>(e);
+            }
+        }
+    }
+}
+
 static int ilog2(int64_t v) {
     int r = 0;
     while ((int64_t(1) << r) < v) r++;
@@ -354,6 +404,15 @@ extern "C" knn_status knn_join_build_index(const knn_csr* S, const knn_build_opt
         else
             k_scatter<float><<<wblocks, 256, 0, stream>>>(ix->s_indptr, ix->sp_d, (const float*)spw, bucket,
                                                          bp, cursor, post);
+        BAIL_CUDA(cudaGetLastError());
+        count_launch();
+        const int64_t n_lists = (int64_t)ix->n_blocks * s.dim;
+        if (s.dtype == KNN_U8)
+            k_arrange<uint32_t, 4><<<launch_blocks(n_lists, 128), 128, 0, stream>>>(ix->binoff, n_lists, nl,
+                                                                                     (uint32_t*)post);
+        else
+            k_arrange<uint2, 2><<<launch_blocks(n_lists, 128), 128, 0, stream>>>(ix->binoff, n_lists, nl,
+                                                                                  (uint2*)post);
         BAIL_CUDA(cudaGetLastError());
         count_launch();
     }
