@@ -3,17 +3,14 @@ fp64 references, training, and the learned join's exactness (verify-and-fallback
 import numpy as np
 import pytest
 
+from oracle import learned as L
 from paper_1011_2807_gb300 import synth
 import compare
 
 pytestmark = pytest.mark.gpu
 
-W1_SHAPE = (256, 528)
-OFF_B1 = 256 * 528
-OFF_W2 = OFF_B1 + 256
-OFF_B2 = OFF_W2 + 256 * 256
-OFF_W3 = OFF_B2 + 256
-OFF_B3 = OFF_W3 + 256
+W1_SHAPE = (L.HID, L.IN_PAD)
+OFF_B1, OFF_W2, OFF_B2, OFF_W3, OFF_B3 = L.OFF_B1, L.OFF_W2, L.OFF_B2, L.OFF_W3, L.OFF_B3
 
 
 @pytest.fixture(scope="module")
@@ -24,11 +21,6 @@ def knn():
     import paper_1011_2807_gb300 as knn
     knn.lib()
     return knn
-
-
-def bf16_round(a):
-    import torch
-    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
 
 
 # ----------------------------------------------------------------------------------
@@ -61,36 +53,12 @@ def test_gemm_bf16(knn, M, N, K, ta, tb):
 # sketch
 # ----------------------------------------------------------------------------------
 
-def mix32(x):
-    x = x.astype(np.uint64) & 0xFFFFFFFF
-    x ^= x >> 16
-    x = (x * 0x85EBCA6B) & 0xFFFFFFFF
-    x ^= x >> 13
-    x = (x * 0xC2B2AE35) & 0xFFFFFFFF
-    x ^= x >> 16
-    return x
-
-
-def sketch_ref(R, model_seed):
-    seed = (model_seed ^ 0x5BD1E995) & 0xFFFFFFFF
-    out = np.zeros((R.n_rows, 528))
-    for i in range(R.n_rows):
-        d, w = R.row(i)
-        w = w.astype(np.float64)
-        norm = np.sqrt((w * w).sum())
-        h = mix32((d.astype(np.uint64) * 0x9E3779B1 + seed) & 0xFFFFFFFF)
-        sign = np.where(h >> 31, -1.0, 1.0)
-        np.add.at(out[i], (h & 511).astype(np.int64), sign * w / norm)
-        out[i, 512:516] = np.log1p([len(d), w.sum(), norm, w.max()])
-    return out
-
-
 def test_sketch(knn):
     R = synth.spectrum_u8(64, 301, role="R")
     m = knn.ThresholdModel(seed=17)
     X = m.sketch(knn.DeviceCSR.from_host(R)).float().cpu().numpy()
-    ref = sketch_ref(R, 17)
-    np.testing.assert_allclose(X, bf16_round(ref), rtol=1e-2, atol=2e-3)
+    ref = L.sketch(R, 17)
+    np.testing.assert_allclose(X, L.bf16_round(ref), rtol=1e-2, atol=2e-3)
     assert (X[:, 516:] == 0).all()
     m.close()
 
@@ -100,47 +68,7 @@ def test_sketch(knn):
 # ----------------------------------------------------------------------------------
 
 def mlp_ref(p, x, t, q, round_like_gpu=True):
-    """fp64 forward and gradients of the mean pinball loss at quantile q."""
-    rb = bf16_round if round_like_gpu else (lambda a: np.asarray(a, np.float64))
-    W1 = rb(p[:OFF_B1].reshape(W1_SHAPE))
-    b1 = p[OFF_B1:OFF_W2].astype(np.float64)
-    W2 = rb(p[OFF_W2:OFF_B2].reshape(256, 256))
-    b2 = p[OFF_B2:OFF_W3].astype(np.float64)
-    w3 = rb(p[OFF_W3:OFF_B3])
-    b3 = float(p[OFF_B3])
-    B = x.shape[0]
-    H1 = rb(np.maximum(x @ W1.T + b1, 0.0))
-    H2 = rb(np.maximum(H1 @ W2.T + b2, 0.0))
-    y = H2 @ w3 + b3
-    e = t - y
-    loss = np.where(e > 0, q * e, (q - 1) * e).mean()
-    g = np.where(e > 0, -q, 1 - q) / B
-    dw3 = g @ H2
-    db3 = g.sum()
-    dH2 = rb(np.outer(g, w3) * (H2 > 0))
-    db2 = dH2.sum(0)
-    dW2 = dH2.T @ H1
-    dH1 = rb((dH2 @ W2) * (H1 > 0))
-    db1 = dH1.sum(0)
-    dW1 = dH1.T @ x
-    grads = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dw3, [db3]])
-    return y, grads, loss
-
-
-def test_reference_backward_matches_finite_differences():
-    rng = np.random.default_rng(0)
-    p = rng.normal(0, 0.05, size=OFF_B3 + 1)
-    x = rng.normal(0, 1, size=(6, 528))
-    x[:, 516:] = 0
-    t = rng.normal(0, 1, size=6)
-    _, g, _ = mlp_ref(p, x, t, 0.3, round_like_gpu=False)
-    for idx in [5, 528 * 3 + 7, OFF_B1 + 9, OFF_W2 + 1000, OFF_B2 + 3, OFF_W3 + 11, OFF_B3]:
-        h = 1e-6
-        pp, pm = p.copy(), p.copy()
-        pp[idx] += h
-        pm[idx] -= h
-        fd = (mlp_ref(pp, x, t, 0.3, False)[2] - mlp_ref(pm, x, t, 0.3, False)[2]) / (2 * h)
-        assert abs(fd - g[idx]) <= 1e-6 + 1e-4 * abs(g[idx]), (idx, fd, g[idx])
+    return L.mlp_forward_backward(p, x, t, q, round_bf16=round_like_gpu)
 
 
 @pytest.mark.parametrize("q", [0.1, 0.5])
@@ -261,10 +189,7 @@ def test_calibrate_picks_the_ratio_quantile(knn, trained):
     scale = m.calibrate(V, kth, 0.05)
     pred = m.predict(V).cpu().numpy()
     kk = kth.cpu().numpy()
-    ratio = np.full(len(kk), np.inf, dtype=np.float32)
-    ok = (kk > 0) & (pred > 0)
-    ratio[ok] = kk[ok] / pred[ok]
-    expect = np.sort(ratio)[int(np.floor(0.05 * len(ratio)))]
+    expect = L.calibrated_scale(kk, pred, 0.05)
     assert abs(scale - expect) <= 1e-5 * expect, (scale, expect)
     assert (pred * scale > kk).mean() <= 0.05 + 1e-9
     # the multiplier travels with the parameters and is the learned join's default
