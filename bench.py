@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--n-train", type=int, default=20000, help="training queries of the learned threshold")
     ap.add_argument("--batch-jobs", type=int, default=64)
+    ap.add_argument("--no-bf", action="store_true", help="skip the brute-force comparison")
+    ap.add_argument("--bf-rows", type=int, default=5000, help="R rows of the brute-force comparison")
     return ap.parse_args()
 
 
@@ -323,6 +325,25 @@ def batched_leg(args, R, S, reps):
                         "S = leading rows of the benchmark S, R = windows of the benchmark R"}
 
 
+def bf_leg(args, R, idx, reps):
+    """Brute force (Algorithm 2 on the GPU: every s scored in full) against the plain join,
+    on the first rows of the benchmark R; the paper compares IIB/IIIB with it."""
+    import torch
+    import paper_1011_2807_gb300 as knn
+    n = min(args.bf_rows, R.n_rows)
+    Rs = knn.DeviceCSR.from_host(R.slice_rows(0, n))
+    k = args.k
+    kw = dict(threads=args.threads, skip_validation=True)
+    pids, psc = knn.knn_join(idx, Rs, k, mode=args.mode, **kw)
+    bids, bsc = knn.knn_join(idx, Rs, k, mode="bf", **kw)
+    torch.cuda.synchronize()
+    identical = bool(torch.equal(pids, bids) and torch.equal(psc, bsc))
+    plain_ms = time_events(lambda: knn.knn_join(idx, Rs, k, mode=args.mode, **kw), reps)
+    bf_ms = time_events(lambda: knn.knn_join(idx, Rs, k, mode="bf", **kw), reps)
+    return {"rows": n, "bf_rows_per_s": n / (bf_ms / 1e3), "plain_rows_per_s": n / (plain_ms / 1e3),
+            "plain_over_bf": bf_ms / plain_ms, "identical": identical, "plain_mode": args.mode}
+
+
 def learned_leg(args, R, S, idx, Rd, ids, sc, plain_ms, reps):
     """Learned start threshold: train on exact k-th scores of fresh queries from the same
     generator, then join the benchmark R from the predictions (verify-and-fallback)."""
@@ -474,7 +495,9 @@ def run_ours(args):
     if traffic_note:
         roofline["traffic_note"] = traffic_note
 
-    batched = learned = None
+    batched = learned = bf = None
+    if rank == 0 and world == 1 and not args.no_bf:
+        bf = bf_leg(args, R, idx, reps=2)
     if rank == 0 and world == 1 and not args.no_learned:
         learned = learned_leg(args, R, S, idx, Rd, ids, sc, kern_ms, reps=3)
     if rank == 0 and world == 1 and not args.no_batched:
@@ -503,7 +526,7 @@ def run_ours(args):
                            "parallelism": f"R rows split over {world} GPU(s), index replicated"},
                 "gpu_launches": launches, "roofline": roofline, "clocks": clk,
                 "e2e": e2e, "cpu_baseline": cpu, "learned_vs_plain": learned, "batched_vs_plain": batched,
-                "kernel_ms_per_step": kern_ms}
+                "bf_vs_plain": bf, "kernel_ms_per_step": kern_ms}
         print(json.dumps(line), flush=True)
     idx.close()
     if world > 1:

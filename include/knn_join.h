@@ -139,7 +139,10 @@ void knn_index_destroy(knn_index* index);
 
 typedef enum {
     KNN_MODE_IIIB = 0,    /* threshold-refined scan (Section 4.4), the default        */
-    KNN_MODE_IIB = 1      /* every list scanned whole (Section 4.3)                   */
+    KNN_MODE_IIB = 1,     /* every list scanned whole (Section 4.3)                   */
+    KNN_MODE_BF = 2       /* brute force (Algorithm 2), a baseline: every s of each S
+                             block scored in full against r; same results, no posting
+                             scan.  knn_join only (not the batched form).            */
 } knn_mode;
 
 typedef struct {

@@ -22,7 +22,15 @@ LIB_PATH = os.path.join(_PKG, "libknnjoin.so")
 
 KNN_OK, KNN_EINVAL, KNN_ENOMEM, KNN_ECUDA, KNN_ETIMEOUT, KNN_EUNSUPPORTED = range(6)
 KNN_U8, KNN_F32 = 0, 1
-KNN_MODE_IIIB, KNN_MODE_IIB = 0, 1
+KNN_MODE_IIIB, KNN_MODE_IIB, KNN_MODE_BF = 0, 1, 2
+_MODES = {"iiib": KNN_MODE_IIIB, "iib": KNN_MODE_IIB, "bf": KNN_MODE_BF}
+
+
+def _mode(mode: str) -> int:
+    try:
+        return _MODES[mode]
+    except KeyError:
+        raise ValueError(f"mode must be one of {sorted(_MODES)}") from None
 KNN_MAX_K = 64
 
 
@@ -271,7 +279,7 @@ def knn_join(index: Index, R, k: int, *, mode: str = "iiib", threads: int = 0, s
         else:
             out_ids = torch.empty((n, k), dtype=torch.int32, device="cuda")
             out_scores = torch.empty((n, k), dtype=sdt, device="cuda")
-    opts = _JoinOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), int(s_groups),
+    opts = _JoinOpts(_mode(mode), int(threads), int(s_groups),
                      _ptr(init_threshold), _ptr(n_found), _ptr(postings_scanned),
                      int(bool(outputs_on_host)), int(bool(skip_validation)), float(level_margin),
                      _ptr(stats), int(blocks_per_launch))
@@ -299,7 +307,7 @@ def knn_join_noalloc(index: Index, R: DeviceCSR, k: int, out_ids: torch.Tensor, 
         raise TypeError("knn_join_noalloc needs a DeviceCSR on the GPU")
     keep = []
     c = _csr(R, keep)
-    opts = _JoinOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), 1,
+    opts = _JoinOpts(_mode(mode), int(threads), 1,
                      _ptr(init_threshold), _ptr(n_found), None, 0, int(bool(skip_validation)),
                      float(level_margin), None, int(blocks_per_launch))
     _check(L, L.knn_join_noalloc(index.handle, ctypes.byref(c), int(k), ctypes.byref(opts),
@@ -495,7 +503,7 @@ def knn_join_learned(index: Index, model: "ThresholdModel | None", R, k: int, *,
     if out_ids is None:
         out_ids = torch.empty((n, k), dtype=torch.int32, device="cuda")
         out_scores = torch.empty((n, k), dtype=sdt, device="cuda")
-    jo = _JoinOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), int(s_groups), None, None,
+    jo = _JoinOpts(_mode(mode), int(threads), int(s_groups), None, None,
                    _ptr(postings_scanned), 0, 0, float(level_margin), _ptr(stats_out), int(blocks_per_launch))
     lo = _LearnedOpts(jo, float(tau_scale), _ptr(tau))
     st = _LearnedStats()
@@ -572,7 +580,7 @@ class Batch:
         self._keep = []
         arr, self.outputs = _jobs_array(jobs, self._keep)
         self._keep.append(arr)
-        o = _BatchOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), int(blocks_per_group),
+        o = _BatchOpts(_mode(mode), int(threads), int(blocks_per_group),
                        float(level_margin), int(bool(use_graph)), int(bool(skip_validation)), _ptr(stats),
                        int(wait_spins), int(bool(test_never_publish)))
         h = ctypes.c_void_p()
@@ -612,7 +620,7 @@ def knn_join_batched(jobs, *, mode="iiib", threads=0, blocks_per_group=0, level_
     L = _batch_lib()
     keep = []
     arr, outs = _jobs_array(jobs, keep)
-    o = _BatchOpts(KNN_MODE_IIB if mode == "iib" else KNN_MODE_IIIB, int(threads), int(blocks_per_group),
+    o = _BatchOpts(_mode(mode), int(threads), int(blocks_per_group),
                    float(level_margin), 0, 0, None, 0, 0)
     _check(L, L.knn_join_batched(len(jobs), arr, ctypes.byref(o), _stream_ptr(stream)))
     return outs

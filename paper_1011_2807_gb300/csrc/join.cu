@@ -150,6 +150,7 @@ struct JoinParams {
     const uint32_t* ubound;
     float levels[KNN_MAX_LEVELS];
     int32_t k, groups, blocks_per_group, iiib, max_r_nnz;
+    int32_t bf;         // brute force: every s scored in full (Algorithm 2), no posting scan
     float level_margin;
     int32_t rden_dim;   // >0: r's uint8 weights are kept densely (rden_dim bytes, a multiple of 16)
     const float* init_thr;
@@ -376,7 +377,7 @@ __device__ __forceinline__ void prepare_block_warp(const JoinParams& p, const in
     if (lane == 0) ipre[rn] = carry;
 }
 
-template <class W, bool COUNT>
+template <class W, bool COUNT, bool BF>
 __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row, const int g, const int b0,
                                          const int b1, const bool carry_in, const int out_mode,
                                          unsigned char* smem) {
@@ -553,7 +554,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                 st.floor = fl;
                 st.theta = theta;
                 st.level = level;
-                st.need_prepare = st.pred_level != level;
+                st.need_prepare = !BF && st.pred_level != level;
                 st.pending = 0;
                 st.n_steps++;
                 st.lb = st.lbnd[level];
@@ -584,11 +585,29 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         const bool producer = nwarps >= 4;
         if (producer && warp == 0) {
             drain();   // the previous block's deferred candidates
-            if (b + 1 < b1)
+            if (b + 1 < b1 && !BF)
                 prepare_block_warp<V, CH>(p, rf_d, rn, b + 1, level, lbeg_buf + ((b + 1) & 1) * p.max_r_nnz,
                                           lend_buf + ((b + 1) & 1) * p.max_r_nnz,
                                           ipre_buf + ((b + 1) & 1) * (p.max_r_nnz + 1), lane);
             if (lane == 0) st.pred_level = b + 1 < b1 ? level : -1;
+        } else if (BF) {
+            // Algorithm 2 on the GPU (a baseline): every s of the block is scored in full
+            // against r, whose weights are read from the dense copy in shared memory (or by
+            // binary search in r's sorted features); each entry is written once.
+            const int t0 = producer ? 32 : 0;
+            const int64_t s0 = (int64_t)b << p.block_shift;
+            const int ns = (int)min((int64_t)nb, p.n_s - s0);
+            for (int lid = tid - t0; lid < ns; lid += T - t0) {
+                const int64_t a = p.s_indptr[s0 + lid], e = p.s_indptr[s0 + lid + 1];
+                Acc sum = (Acc)0;
+                for (int64_t j = a; j < e; j++) {
+                    const int32_t d = p.sp_d[j];
+                    const Acc w = (Acc)((const W*)p.sp_w)[j];
+                    sum += (rden ? (Acc)rden[d] : lookup_r<W>(rf_d, rf_w, rn, d)) * w;
+                }
+                acc[lid] = sum;
+                if (COUNT) n_post += (unsigned long long)(e - a);
+            }
         } else {
             const Post* post = (const Post*)p.postings;
             const int t0 = producer ? 32 : 0;
@@ -886,25 +905,29 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     }
 }
 
-template <class W, bool COUNT>
+template <class W, bool COUNT, bool BF>
 __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int64_t row = blockIdx.x / p.groups;
     const int g = blockIdx.x - (int)(row * p.groups);
     if (p.groups == 1)
-        join_row<W, COUNT>(p, row, 0, p.block_begin, p.block_end, p.carry_in != 0,
+        join_row<W, COUNT, BF>(p, row, 0, p.block_begin, p.block_end, p.carry_in != 0,
                            p.carry_out ? OUT_CARRY : OUT_FINAL, smem);
     else
-        join_row<W, COUNT>(p, row, g, g * p.blocks_per_group, min(p.n_blocks, (g + 1) * p.blocks_per_group), false,
+        join_row<W, COUNT, BF>(p, row, g, g * p.blocks_per_group, min(p.n_blocks, (g + 1) * p.blocks_per_group), false,
                            OUT_GROUP, smem);
 }
 
 // The posting count (stats, eq. 4 checks) costs a compare per posting, so it is
 // compiled into a separate instance that runs only when a counter is requested.
 using JoinKernel = void (*)(JoinParams);
-static JoinKernel join_kernel(knn_dtype dt, bool count) {
-    if (dt == KNN_U8) return count ? k_join<uint8_t, true> : k_join<uint8_t, false>;
-    return count ? k_join<float, true> : k_join<float, false>;
+static JoinKernel join_kernel(knn_dtype dt, bool count, bool bf) {
+    if (bf) {
+        if (dt == KNN_U8) return count ? k_join<uint8_t, true, true> : k_join<uint8_t, false, true>;
+        return count ? k_join<float, true, true> : k_join<float, false, true>;
+    }
+    if (dt == KNN_U8) return count ? k_join<uint8_t, true, false> : k_join<uint8_t, false, false>;
+    return count ? k_join<float, true, false> : k_join<float, false, false>;
 }
 
 
@@ -971,7 +994,7 @@ __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ B
         __syncthreads();
         if (g > 0 && !s_ok) continue;
         const bool last = g == J.groups - 1;
-        join_row<W, COUNT>(J, row, g, g * J.blocks_per_group, min(J.n_blocks, (g + 1) * J.blocks_per_group),
+        join_row<W, COUNT, false>(J, row, g, g * J.blocks_per_group, min(J.n_blocks, (g + 1) * J.blocks_per_group),
                            g > 0, last ? OUT_FINAL : OUT_CARRY, smem);
         if (!last && !no_publish) {   // publish: the carried keys are in global memory before the flag
             __syncthreads();
@@ -1025,7 +1048,8 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     if (R->dtype != ix->dtype) return fail(KNN_EINVAL, "R and the index have different dtypes");
     knn_join_opts o = {};
     if (opts) o = *opts;
-    if (o.mode != KNN_MODE_IIIB && o.mode != KNN_MODE_IIB) return fail(KNN_EINVAL, "unknown mode");
+    if (o.mode != KNN_MODE_IIIB && o.mode != KNN_MODE_IIB && o.mode != KNN_MODE_BF)
+        return fail(KNN_EINVAL, "unknown mode");
     if (R->n_rows > 0 && (!out_ids || !out_scores)) return fail(KNN_EINVAL, "outputs are NULL");
 
     Buffers tmp(stream);
@@ -1106,6 +1130,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     p.groups = groups;
     p.blocks_per_group = bpg;
     p.iiib = o.mode == KNN_MODE_IIIB && ix->n_levels > 1;
+    p.bf = o.mode == KNN_MODE_BF;
     p.max_r_nnz = max_r;
     p.rden_dim = rden_dim;
     p.init_thr = o.init_threshold;
@@ -1122,7 +1147,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
         KNN_CUDA_TRY(cudaMemsetAsync(p.floor_keys, 0, sizeof(u64) * r.n_rows, stream));
     }
     int64_t grid = r.n_rows * groups;
-    const JoinKernel kern = join_kernel(ix->dtype, p.touched || p.stats);
+    const JoinKernel kern = join_kernel(ix->dtype, p.touched || p.stats, p.bf != 0);
     KNN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     // One group per row: S-block-synchronous launches.  Every launch walks all rows over
     // the same few S blocks, so their postings stay in L2 while all rows read them.
@@ -1215,7 +1240,8 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     if (!R->on_device) return fail(KNN_EINVAL, "knn_join_noalloc needs R in device memory (on_device = 1)");
     knn_join_opts o = {};
     if (opts) o = *opts;
-    if (o.mode != KNN_MODE_IIIB && o.mode != KNN_MODE_IIB) return fail(KNN_EINVAL, "unknown mode");
+    if (o.mode != KNN_MODE_IIIB && o.mode != KNN_MODE_IIB && o.mode != KNN_MODE_BF)
+        return fail(KNN_EINVAL, "unknown mode");
     if (o.outputs_on_host) return fail(KNN_EINVAL, "knn_join_noalloc writes device outputs only");
     if (R->n_rows > 0 && (!out_ids || !out_scores)) return fail(KNN_EINVAL, "outputs are NULL");
     const size_t carry_cap = (KNN_NOALLOC_SCRATCH_BYTES - NOALLOC_HEADER) / sizeof(u64);
@@ -1280,6 +1306,7 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     p.groups = 1;   // one group per row: the only schedule whose scratch is the carry buffer
     p.blocks_per_group = ix->n_blocks;
     p.iiib = o.mode == KNN_MODE_IIIB && ix->n_levels > 1;
+    p.bf = o.mode == KNN_MODE_BF;
     p.max_r_nnz = max_r;
     p.rden_dim = rden_dim;
     p.init_thr = o.init_threshold;
@@ -1292,7 +1319,7 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     if (!(p.level_margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     p.carry = (u64*)((unsigned char*)scratch + NOALLOC_HEADER);
 
-    const JoinKernel kern = join_kernel(ix->dtype, p.touched || p.stats);
+    const JoinKernel kern = join_kernel(ix->dtype, p.touched || p.stats, p.bf != 0);
     KNN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     const int per_launch = std::min(ix->n_blocks, o.blocks_per_launch > 0 ? o.blocks_per_launch : 8);
     const int n_launch = (int)ceil_div(ix->n_blocks, per_launch);

@@ -303,6 +303,48 @@ def test_posting_counter_eq4(knn):
 
 
 # ----------------------------------------------------------------------------------
+# brute force (Algorithm 2) on the GPU: the baseline mode gives the same results
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bs,groups", [(256, 0), (1024, 1), (2048, 3)])
+@pytest.mark.parametrize("k", [1, 5, 64])
+def test_bf_mode_u8_exact(knn, oracle_mod, bs, groups, k):
+    S = synth.spectrum_u8(5000, 131, role="S")          # ragged last block
+    R = synth.spectrum_u8(90, 132, role="R")
+    eids, esc, _ = oracle_mod.bf_join(R, S, k, threads=8)
+    ids, sc = run(knn, S, R, k, mode="bf", block_size=bs, s_groups=groups)
+    compare.assert_exact(ids, sc, eids, esc, f"bf bs={bs} groups={groups} k={k}")
+
+
+def test_bf_mode_f32_and_degenerate(knn, oracle_mod):
+    S = synth.zipf_f32(3000, 141, dim=2000, nnz_hi=200)
+    R = synth.zipf_f32(40, 142, dim=2000, nnz_hi=200)
+    eids, esc, _ = oracle_mod.bf_join(R, S, 20, threads=8)
+    ids, sc = run(knn, S, R, 20, mode="bf", block_size=512)
+    compare.assert_close(R, S, list(range(R.n_rows)), ids, sc, eids, esc, what="bf f32")
+    S2 = synth.from_rows([[(1, 2), (3, 1)], [], [(3, 2)], [(2, 4)], [(1, 1), (3, 1)]], 6)
+    R2 = synth.from_rows([[], [(0, 9)], [(1, 1), (3, 1)]], 6)
+    ids, sc = run(knn, S2, R2, 7, mode="bf")
+    eids, esc, _ = oracle_mod.bf_join(R2, S2, 7)
+    compare.assert_exact(ids, sc, eids, esc, "bf degenerate")
+
+
+def test_bf_mode_reads_every_feature_of_s(knn):
+    """The brute-force work counter is nnz(S) per non-empty query row (every S vector is
+    scored in full, eq. 3's S-side term), whatever the block size."""
+    import torch
+    S = synth.spectrum_u8(6000, 151, role="S")
+    R = synth.spectrum_u8(50, 152, role="R")
+    idx = knn.knn_join_build_index(S, block_size=1024)
+    c = torch.zeros(1, dtype=torch.int64, device="cuda")
+    knn.knn_join(idx, knn.DeviceCSR.from_host(R), 5, mode="bf", postings_scanned=c)
+    torch.cuda.synchronize()
+    nonempty = int((np.diff(R.indptr) > 0).sum())
+    assert int(c.item()) == nonempty * S.nnz
+    idx.close()
+
+
+# ----------------------------------------------------------------------------------
 # the benchmark's configuration at full size, on sampled rows
 # ----------------------------------------------------------------------------------
 
