@@ -164,7 +164,7 @@ typedef struct {
     int64_t* stats;             /* device int64[KNN_STATS_LEN] or NULL: work counters,
                                    added to (see KNN_STAT_*)                              */
     int32_t blocks_per_launch;  /* with one group per row: S blocks per kernel launch;
-                                   every launch covers all rows (0 = 8)                    */
+                                   every launch covers all rows (0 = 16)                   */
 } knn_join_opts;
 
 /* Work counters of knn_join (indices into knn_join_opts.stats). */

@@ -22,7 +22,7 @@ import numpy as np
 
 _lock = threading.Lock()
 
-DEFAULT = {"block_size": 16384, "threads": 512, "blocks_per_launch": 8, "level_margin": 0.4}
+DEFAULT = {"block_size": 16384, "threads": 512, "blocks_per_launch": 16, "level_margin": 0.4}
 MARGINS = (0.25, 0.4, 0.55)
 
 

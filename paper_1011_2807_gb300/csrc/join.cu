@@ -214,7 +214,8 @@ struct CtaState {
     int cnt;        // pushed candidates in the sort buffer
     int size;       // entries in topk
     int level;
-    int pending;    // candidates still masked (overflow rounds)
+    int pending[2]; // candidates still masked (overflow rounds), by S block parity: warp 0
+                    // resets the next block's count while others may still read this one
     double theta;   // pruning threshold of the current block
     u64 floor;      // keys below this never qualify
     u64 kth;        // current k-th key (0 while fewer than k)
@@ -555,7 +556,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                 st.theta = theta;
                 st.level = level;
                 st.need_prepare = !BF && st.pred_level != level;
-                st.pending = 0;
+                st.pending[b & 1] = 0;
                 st.n_steps++;
                 st.lb = st.lbnd[level];
                 JT<W>::set_cmin(st, JT<W>::cheap_min(theta, st.lb));
@@ -663,6 +664,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         const int64_t gbase = (int64_t)b << p.block_shift;
         unsigned long long mask = 0ull;
         int mycount = 0;
+#pragma unroll 8
         for (int c = 0; c < chunks; c++) {
             int lid0 = c * T * 4 + tid * 4;
             int4 raw = ld_shared_v4(acc_s + 4u * lid0);
@@ -686,9 +688,10 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         // total candidates of the block
         int wsum = mycount;
         for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-        if (lane == 0 && wsum) atomicAdd(&st.pending, wsum);
+        int& pending = st.pending[b & 1];
+        if (lane == 0 && wsum) atomicAdd(&pending, wsum);
         __syncthreads();
-        const int pend = st.pending;   // most blocks, once the threshold has settled, have none
+        const int pend = pending;   // most blocks, once the threshold has settled, have none
         if (pend > 0 && producer && pend <= CQ_CAP) {
             // Few candidates: queue them for warp 0, which completes and merges them during
             // the next block's scan.  That block's threshold is then one block stale, which
@@ -703,7 +706,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
             }
             if (tid == 0) st.dq_level = level;
         } else if (pend > 0) {
-        if (st.pending > PUSH_CAP) {
+        if (pending > PUSH_CAP) {
             // Too many candidates for one merge (typically the first block, where the
             // threshold is still 0).  Radix-select, on the candidates' partial scores,
             // a value t with at least k candidates >= t and at most PUSH_CAP of them;
@@ -789,11 +792,11 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
             if (tid == 0) {
                 unsigned long long t = 0;
                 for (int w = 0; w < nwarps; w++) t += red_u[w];
-                st.pending = (int)t;
+                pending = (int)t;
             }
             __syncthreads();
         }
-        const bool one_round = st.pending <= PUSH_CAP;
+        const bool one_round = pending <= PUSH_CAP;
         const int per_round = one_round ? 64 : max(1, PUSH_CAP / T);
         while (true) {
             const u64 kth = st.kth;
@@ -863,11 +866,14 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
             if (!more) break;
             if (tid == 0) st.n_rounds++;
         }
-        }   // st.pending > 0
+        }   // pend > 0
         // publish this group's k-th key as a floor for the other groups of the row
         if (tid == 0 && p.floor_keys && st.size == p.k) atomicMax(p.floor_keys + row, st.kth);
-        __syncthreads();
+        // No barrier here: the next block's step 1 (warp 0) writes only state no other warp
+        // reads after this block's select barrier (the candidate count is double-buffered),
+        // and its barrier orders this block's deferred pushes before warp 0 drains them.
     }
+    __syncthreads();
     if (nwarps >= 4) {   // the last block's deferred candidates
         if (warp == 0) drain();
         __syncthreads();
@@ -1151,7 +1157,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     KNN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     // One group per row: S-block-synchronous launches.  Every launch walks all rows over
     // the same few S blocks, so their postings stay in L2 while all rows read them.
-    int per_launch = groups == 1 ? (o.blocks_per_launch > 0 ? o.blocks_per_launch : 8) : ix->n_blocks;
+    int per_launch = groups == 1 ? (o.blocks_per_launch > 0 ? o.blocks_per_launch : 16) : ix->n_blocks;
     per_launch = std::min(per_launch, ix->n_blocks);
     const int n_launch = groups == 1 ? (int)ceil_div(ix->n_blocks, per_launch) : 1;
     if (n_launch > 1) KNN_TRY(tmp.get(&p.carry, (size_t)r.n_rows * k));
@@ -1321,7 +1327,7 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
 
     const JoinKernel kern = join_kernel(ix->dtype, p.touched || p.stats, p.bf != 0);
     KNN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-    const int per_launch = std::min(ix->n_blocks, o.blocks_per_launch > 0 ? o.blocks_per_launch : 8);
+    const int per_launch = std::min(ix->n_blocks, o.blocks_per_launch > 0 ? o.blocks_per_launch : 16);
     const int n_launch = (int)ceil_div(ix->n_blocks, per_launch);
     for (int li = 0; li < n_launch; li++) {
         p.block_begin = li * per_launch;
