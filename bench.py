@@ -483,13 +483,16 @@ def run_ours(args):
     bytes_out = R.n_rows * k * 8
     alg_bytes = bytes_post + bytes_r + bytes_out
     kern_ms = statistics.mean(step_ms)
-    achieved = alg_bytes / (kern_ms / 1000.0) / 1e9
+    achieved = alg_bytes / (kern_ms / 1000.0) / 1e9   # = bytes per launch / mean launch time
+    launches_per_step = max(1, launches // max(1, args.steps))
     traffic, traffic_note = profiled_traffic(os.path.join(ROOT, "paper_1011_2807_gb300", "csrc", "join.cu"))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_join (posting scan + accumulate + select + top-k, fused)",
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_launch": alg_bytes,
+                "algorithmic_bytes_per_step": alg_bytes, "kernel_launches_per_step": launches_per_step,
+                "algorithmic_bytes_per_launch": alg_bytes / launches_per_step,
+                "traffic_unit": "DRAM bytes read + written per k_join launch (ncu, full-size launch)",
                 "bytes_per_unit": "4 B per posting scanned + 5 B per R feature + 8 B per R row index + 8k B output",
                 "iib_equivalent_GBps": (4 * p_iib + bytes_r + bytes_out) / (kern_ms / 1000.0) / 1e9}
     if traffic_note:
