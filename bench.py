@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--n-train", type=int, default=20000, help="training queries of the learned threshold")
     ap.add_argument("--batch-jobs", type=int, default=64)
     ap.add_argument("--no-bf", action="store_true", help="skip the brute-force comparison")
+    ap.add_argument("--no-float", action="store_true", help="skip the float scale-up leg")
+    ap.add_argument("--float-s", type=int, default=500000, help="|S| of the float scale-up leg")
+    ap.add_argument("--float-r", type=int, default=10000, help="|R| of the float scale-up leg")
     ap.add_argument("--bf-rows", type=int, default=5000, help="R rows of the brute-force comparison")
     return ap.parse_args()
 
@@ -344,6 +347,66 @@ def bf_leg(args, R, idx, reps):
             "plain_over_bf": bf_ms / plain_ms, "identical": identical, "plain_mode": args.mode}
 
 
+def float_leg(args, reps):
+    """The float scale-up's shape (Zipf(1.1) ids over d = 50,000, power-law nnz in
+    [5, 2000], L2-normalised log-normal weights, k = 20) at reduced |S| and |R|: the plain
+    join in IIB and IIIB form, the learned form (trained and calibrated on queries of the
+    same generator) and a batched launch of the rows split into 8 uneven jobs, each
+    against the plain IIIB join on the same rows."""
+    import torch
+    import paper_1011_2807_gb300 as knn
+    from paper_1011_2807_gb300 import synth
+    k = 20
+    t0 = time.perf_counter()
+    S = synth.zipf_f32(args.float_s, synth.config_seed(5, "S"))
+    R = synth.zipf_f32(args.float_r, synth.config_seed(5, "R"))
+    A = synth.zipf_f32(12000, synth.config_seed(5, "train"))
+    gen_s = time.perf_counter() - t0
+    idx = knn.knn_join_build_index(S)
+    Rd = knn.DeviceCSR.from_host(R)
+    out = {"workload": f"|R|={R.n_rows:,}, |S|={S.n_rows:,} (nnz {S.nnz:,}), d=50,000, Zipf(1.1) ids, "
+                       f"power-law nnz [5, 2000], L2-normalised lognormal float32, k=20",
+           "generate_s": gen_s}
+    ref_ids, ref_sc = knn.knn_join(idx, Rd, k)
+    torch.cuda.synchronize()
+    for name, kw in (("iib", dict(mode="iib")), ("iiib", dict(mode="iiib")),
+                     ("iiib_margin_0.25", dict(mode="iiib", level_margin=0.25))):
+        ms = time_events(lambda: knn.knn_join(idx, Rd, k, skip_validation=True, **kw), reps)
+        out[name + "_rows_per_s"] = R.n_rows / (ms / 1e3)
+    plain_ms = time_events(lambda: knn.knn_join(idx, Rd, k, skip_validation=True), reps)
+    # learned: 9,000 training and 3,000 calibration queries
+    Ad = knn.DeviceCSR.from_host(A)
+    _, asc = knn.knn_join(idx, Ad, k)
+    kth = asc[:, k - 1].float()
+    model = knn.ThresholdModel(seed=5)
+    model.train(A.slice_rows(0, 9000), kth[:9000].contiguous(), epochs=15, batch=512, quantile=0.1, seed=5)
+    scale = model.calibrate(A.slice_rows(9000, A.n_rows), kth[9000:].contiguous(), 0.002)
+    res = {}
+    l_ms = time_events(lambda: res.update(o=knn.knn_join_learned(idx, model, Rd, k)), reps)
+    lids, lsc, lst = res["o"]
+    # float scores: the learned form returns the same ids and scores as the plain join
+    # up to summation order; count rows whose ids differ
+    out["learned"] = {"speedup": plain_ms / l_ms, "fallback_rate": lst["fallback_rows"] / R.n_rows,
+                      "tau_scale": scale,
+                      "rows_with_other_ids": int((lids != ref_ids).any(dim=1).sum().item())}
+    model.close()
+    # batched: the rows in 8 uneven jobs against the same index, one persistent launch
+    cuts = [0] + sorted(int(R.n_rows * f) for f in (0.02, 0.05, 0.1, 0.2, 0.35, 0.55, 0.75)) + [R.n_rows]
+    parts = [knn.DeviceCSR.from_host(R.slice_rows(a, b)) for a, b in zip(cuts[:-1], cuts[1:])]
+    b = knn.Batch([(idx, P, k) for P in parts], use_graph=True, skip_validation=True)
+    b.launch()
+    torch.cuda.synchronize()
+    b_ms = time_events(lambda: b.launch(), reps)
+    sep_ms = time_events(lambda: [knn.knn_join(idx, P, k, skip_validation=True) for P in parts], reps)
+    bids = torch.cat([o[0] for o in b.outputs])
+    out["batched"] = {"jobs": len(parts), "speedup_vs_separate_calls": sep_ms / b_ms,
+                      "rows_with_other_ids": int((bids != ref_ids).any(dim=1).sum().item())}
+    b.close()
+    out["plain_iiib_ms"] = plain_ms
+    idx.close()
+    return out
+
+
 def learned_leg(args, R, S, idx, Rd, ids, sc, plain_ms, reps):
     """Learned start threshold: train on exact k-th scores of fresh queries from the same
     generator, then join the benchmark R from the predictions (verify-and-fallback)."""
@@ -498,13 +561,16 @@ def run_ours(args):
     if traffic_note:
         roofline["traffic_note"] = traffic_note
 
-    batched = learned = bf = None
+    batched = learned = bf = flt = None
     if rank == 0 and world == 1 and not args.no_bf:
         bf = bf_leg(args, R, idx, reps=2)
     if rank == 0 and world == 1 and not args.no_learned:
         learned = learned_leg(args, R, S, idx, Rd, ids, sc, kern_ms, reps=3)
     if rank == 0 and world == 1 and not args.no_batched:
         batched = batched_leg(args, R, S, reps=3)
+
+    if rank == 0 and world == 1 and not args.no_float:
+        flt = float_leg(args, reps=3)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -529,7 +595,7 @@ def run_ours(args):
                            "parallelism": f"R rows split over {world} GPU(s), index replicated"},
                 "gpu_launches": launches, "roofline": roofline, "clocks": clk,
                 "e2e": e2e, "cpu_baseline": cpu, "learned_vs_plain": learned, "batched_vs_plain": batched,
-                "bf_vs_plain": bf, "kernel_ms_per_step": kern_ms}
+                "bf_vs_plain": bf, "float_scaleup": flt, "kernel_ms_per_step": kern_ms}
         print(json.dumps(line), flush=True)
     idx.close()
     if world > 1:

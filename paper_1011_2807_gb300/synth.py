@@ -98,7 +98,7 @@ def from_rows(rows, dim: int, dtype=np.uint8) -> CSR:
 # unique-id sampling: first `nnz[i]` distinct draws in draw order, then sorted
 # ----------------------------------------------------------------------------------
 
-def _unique_rows(rng, nnz, draw, dim, chunk=1 << 18):
+def _unique_rows(rng, nnz, draw, dim, chunk=1 << 18, over=1.3, pos_bits=12):
     """Rejection sampling without replacement, vectorised over rows.
 
     For each row, ids are drawn one after another from ``draw``; a repeat of an id
@@ -114,11 +114,10 @@ def _unique_rows(rng, nnz, draw, dim, chunk=1 << 18):
     indptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(nnz, out=indptr[1:])
     out = np.empty(int(indptr[-1]), dtype=np.int32)
-    pos_bits = 12
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
         need = nnz[a:b]
-        width = min((1 << pos_bits) - 1, max(8, int(int(need.max(initial=0)) * 1.3) + 8))
+        width = min((1 << pos_bits) - 1, max(8, int(int(need.max(initial=0)) * over) + 8))
         ids = draw(rng, (b - a, width)).astype(np.int64)
         key = ids * (1 << pos_bits) + np.arange(width)[None, :]
         key.sort(axis=1)
@@ -155,6 +154,31 @@ def _unique_rows(rng, nnz, draw, dim, chunk=1 << 18):
                         have.append(x)
             r = a + j
             out[indptr[r]:indptr[r + 1]] = np.sort(np.asarray(have[:need[j]], dtype=np.int64))
+    return indptr, out
+
+
+def _unique_rows_by_length(rng, nnz, draw, dim, budget=1 << 23):
+    """:func:`_unique_rows` for heavy-tailed row lengths: rows are visited in ascending
+    nnz order (stable), in chunks of about ``budget`` draws, so each chunk's oversampled
+    batch (2x) is sized by its own longest row.  Returns (indptr, indices) in the
+    original row order, each row's ids sorted ascending."""
+    n = int(nnz.shape[0])
+    nnz = nnz.astype(np.int64)
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(nnz, out=indptr[1:])
+    out = np.empty(int(indptr[-1]), dtype=np.int32)
+    order = np.argsort(nnz, kind="stable")
+    a = 0
+    while a < n:
+        b = a + 1
+        while b < n and (b - a + 1) * (2 * int(nnz[order[b]]) + 8) <= budget:
+            b += 1
+        rows = order[a:b]
+        cptr, cidx = _unique_rows(rng, nnz[rows], draw, dim, chunk=b - a, over=2.0, pos_bits=13)
+        lens = nnz[rows]
+        dst = np.repeat(indptr[rows], lens) + (np.arange(int(lens.sum())) - np.repeat(cptr[:-1], lens))
+        out[dst] = cidx
+        a = b
     return indptr, out
 
 
@@ -247,7 +271,7 @@ def zipf_f32(n: int, seed: int, *, dim: int = 50000, alpha: float = 1.1,
     rng = np.random.default_rng(seed)
     nnz = np.minimum(powerlaw_nnz(rng, n, nnz_lo, nnz_hi), dim)
     perm = np.random.default_rng(config_seed(5, "mix") if perm_seed is None else perm_seed).permutation(dim)
-    indptr, idx = _unique_rows(rng, nnz, _zipf_draw(perm, alpha), dim)
+    indptr, idx = _unique_rows_by_length(rng, nnz, _zipf_draw(perm, alpha), dim)
     w = rng.lognormal(0.0, 1.0, size=idx.shape[0])
     rows = np.repeat(np.arange(n), np.diff(indptr))
     norm = np.sqrt(np.bincount(rows, weights=w * w, minlength=n))

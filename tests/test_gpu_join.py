@@ -168,6 +168,23 @@ def test_zipf_normalised_f32(knn, oracle_mod):
         compare.assert_close(R, S, list(range(R.n_rows)), ids, sc, eids, esc, what=f"zipf {mode}")
 
 
+@pytest.mark.slow
+def test_config5_shaped_f32_sampled_rows(knn, oracle_mod):
+    """The float scale-up's generator (Zipf ids over d = 50,000, power-law nnz up to
+    2,000, L2-normalised log-normal weights, k = 20) at |S| = 150,000 (10 S blocks), on
+    24 query rows, against the fp64 oracle."""
+    S = synth.zipf_f32(150000, synth.config_seed(5, "S"))
+    R = synth.zipf_f32(24, synth.config_seed(5, "R"))
+    eids, esc, _ = oracle_mod.iib_join(R, S, 20, threads=8)
+    idx = knn.knn_join_build_index(S)
+    Rd = knn.DeviceCSR.from_host(R)
+    for mode, margin in (("iib", 0.0), ("iiib", 0.25), ("iiib", 0.6)):
+        ids, sc = knn.knn_join(idx, Rd, 20, mode=mode, level_margin=margin)
+        compare.assert_close(R, S, list(range(R.n_rows)), ids.cpu().numpy(), sc.cpu().numpy(), eids, esc,
+                             what=f"config5-shaped {mode} {margin}")
+    idx.close()
+
+
 # ----------------------------------------------------------------------------------
 # degenerate inputs
 # ----------------------------------------------------------------------------------
