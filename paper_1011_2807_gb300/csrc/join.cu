@@ -313,22 +313,6 @@ __device__ __forceinline__ void st_shared_v4(uint32_t saddr, int4 v) {
                  : "memory");
 }
 
-__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void prefetch_l1(const void* ptr) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(ptr));
-}
-
-__device__ __forceinline__ void prefetch_l2(const void* ptr) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
-}
-
 template <class W>
 __device__ __forceinline__ typename JT<W>::Acc lookup_r(const int32_t* rf_d, const typename JT<W>::Acc* rf_w,
                                                         int n, int32_t d) {
