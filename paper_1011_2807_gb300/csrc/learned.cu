@@ -1,6 +1,7 @@
 // Learned-threshold join with verify-and-fallback.
 //
-// 1. tau = exp(MLP(sketch(r))) per query row (or caller-given thresholds);
+// 1. tau = exp(MLP(sketch(r))) x the model's calibrated multiplier per query row (or
+//    caller-given thresholds);
 // 2. knn_join with tau as each row's inclusive start threshold: a row keeps only the s
 //    with score >= tau, and the Section 4.4 cut starts from tau instead of 0;
 // 3. a row that ends with k entries has its exact top-k (every s with score >= tau was
@@ -8,7 +9,7 @@
 //    than k are gathered on the device and joined again with the plain threshold, and
 //    their results are scattered back.
 // The result is therefore always the exact top-k; the plain join is both the fallback
-// and the judge of the prediction.
+// and the check of the prediction.
 #include <cuda_runtime.h>
 
 #include <algorithm>
