@@ -333,7 +333,9 @@ knn_status knn_join_learned(const knn_index* index, const knn_model* model, cons
 
 /* Test and inspection hooks of the model's kernels (no paper counterpart).
  *   knn_gemm_bf16: C[m*scm + n*scn] (+)= sum_k A[m*sam + k*sak] * B[k*sbk + n*sbn] on
- *     tensor cores (bf16 inputs, fp32 accumulation), all device pointers.
+ *     the tcgen05 tensor cores (bf16 inputs, fp32 accumulation in tensor memory), all
+ *     device pointers; synchronises `stream`; KNN_ETIMEOUT if a bounded wait for the
+ *     tensor core gave up (the model calls report the same).
  *   knn_threshold_sketch: device bf16 [R.n_rows][528] sketches (columns 516.. are 0).
  *   knn_threshold_model_forward_backward: one forward and backward pass on device bf16
  *     inputs x [B][528] and targets (log k-th scores) at a quantile; writes device

@@ -146,6 +146,9 @@ knn_status model_predict_tau(const knn_model* md, const DevCSR& r, float tau_sca
                              Buffers& tmp);
 // The model's calibrated prediction multiplier (1 until knn_threshold_model_calibrate).
 float model_tau_scale(const knn_model* md);
+// KNN_ETIMEOUT if a model GEMM gave up a bounded wait since the last check (the caller
+// has synchronised the stream), else KNN_OK.
+knn_status model_check();
 
 // Exclusive scan of u32 counts (n elements) into out[0..n], out[n] = total.
 // The total must stay below 2^32 (checked by the caller).  Works in place.

@@ -94,6 +94,8 @@ extern "C" knn_status knn_join_learned(const knn_index* ix, const knn_model* md,
     if (!tau) {
         KNN_TRY(tmp.get(&tau, (size_t)r.n_rows));
         KNN_TRY(model_predict_tau(md, r, o.tau_scale > 0.0f ? o.tau_scale : model_tau_scale(md), tau, s, tmp));
+        KNN_CUDA_TRY(cudaStreamSynchronize(s));
+        KNN_TRY(model_check());
     }
     // 2. the join from those thresholds
     int32_t* found = nullptr;

@@ -11,7 +11,7 @@
 // low quantile q, so that exp(y) tends to sit below the true k-th score; the join then
 // keeps every s with score >= exp(y) and verifies that k were found (knn_join_learned).
 //
-// Kernels: k_sketch, k_gemm_bf16 (tensor cores, mma.sync m16n8k16), bias/ReLU,
+// Kernels: k_sketch, k_gemm_bf16 (tcgen05 tensor cores, TMEM accumulator), bias/ReLU,
 // the output layer, the loss gradient, the backward reductions and Adam.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -90,88 +90,173 @@ __global__ void k_sketch(const int64_t* __restrict__ indptr, const int32_t* __re
 }
 
 // ---------------------------------------------------------------------------------
-// BF16 GEMM on tensor cores: C[m][n] (+)= sum_k A(m,k) * B(k,n), FP32 accumulation.
-// A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn] (bf16, any strides), so one
-// kernel serves X W^T, dH W and dH^T X.  CTA tile 64 x 64, K step 32, 4 warps; each
-// warp owns 16 rows x 64 columns = 8 mma.sync.m16n8k16 tiles.
+// BF16 GEMM on the 5th-generation tensor cores: C[m][n] (+)= sum_k A(m,k) * B(k,n) with
+// FP32 accumulation in tensor memory.  A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk +
+// n*sbn] (bf16, any strides), so one kernel serves X W^T, dH W and dH^T X.
+// CTA tile 128 x 64, K step 32.  The operands are staged in shared memory in the
+// canonical K-major layout without swizzle (8 x 8 core matrices of 16-byte rows, the
+// next core matrix along K 128 bytes on, the next 8-row group 512 bytes on); one thread
+// issues tcgen05.mma (kind::f16, M = 128, N = 64, K = 16 each) and commits to an
+// mbarrier, which every thread waits on (bounded) before the tiles are overwritten; at
+// the end each warp reads its 32 accumulator rows (TMEM lanes) with tcgen05.ld.
 // ---------------------------------------------------------------------------------
-constexpr int GM = 64, GN = 64, GK = 32, GKP = GK + 8;
+constexpr int TM = 128, TN = 64, TK = 32;
+constexpr long long GEMM_WAIT_SPINS = 1LL << 22;   // try_wait polls before giving up
+__device__ unsigned g_gemm_err;                     // set when a bounded wait gave up
 
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
+
+// element (r, k) of a [rows][TK] tile in the canonical K-major layout without swizzle
+__device__ __forceinline__ int canon(int r, int k) {
+    return ((r >> 3) * (TK / 8) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+// shared-memory matrix descriptor: start address, leading byte offset (next core matrix
+// along K), stride byte offset (next 8-row group), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B bf16 (bits 7-9 and
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t GEMM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                                ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
 }
 
 __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
                                                    int64_t sam, int64_t sak, const __nv_bfloat16* __restrict__ B,
                                                    int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t scm,
                                                    int64_t scn, int accumulate) {
-    __shared__ __align__(16) __nv_bfloat16 As[GM][GKP];   // [m][k]
-    __shared__ __align__(16) __nv_bfloat16 Bs[GN][GKP];   // [n][k]
+    __shared__ __align__(128) __nv_bfloat16 As[TM * TK];
+    __shared__ __align__(128) __nv_bfloat16 Bs[TN * TK];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
-    float acc[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; j++)
-#pragma unroll
-        for (int q = 0; q < 4; q++) acc[j][q] = 0.0f;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const uint32_t mbar_a = smem_u32(&mbar);
+    if (warp == 0) {   // TN fp32 columns of tensor memory for the 128 x TN accumulator
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_slot)), "n"(TN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
     const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    for (int k0 = 0; k0 < K; k0 += GK) {
-        for (int i = tid; i < GM * GK; i += 128) {
-            int r = i / GK, c = i % GK;
-            int m = m0 + r, k = k0 + c;
-            As[r][c] = (m < M && k < K) ? A[(int64_t)m * sam + (int64_t)k * sak] : zero;
+    uint32_t phase = 0;
+    bool issued = false;
+    for (int k0 = 0; k0 < K; k0 += TK) {
+        for (int i = tid; i < TM * TK; i += 128) {
+            const int r = i / TK, c = i % TK;
+            const int m = m0 + r, k = k0 + c;
+            As[canon(r, c)] = (m < M && k < K) ? A[(int64_t)m * sam + (int64_t)k * sak] : zero;
         }
-        for (int i = tid; i < GN * GK; i += 128) {
-            int r = i / GK, c = i % GK;   // r: n, c: k
-            int n = n0 + r, k = k0 + c;
-            Bs[r][c] = (n < N && k < K) ? B[(int64_t)k * sbk + (int64_t)n * sbn] : zero;
+        for (int i = tid; i < TN * TK; i += 128) {
+            const int r = i / TK, c = i % TK;   // r: n, c: k
+            const int n = n0 + r, k = k0 + c;
+            Bs[canon(r, c)] = (n < N && k < K) ? B[(int64_t)k * sbk + (int64_t)n * sbn] : zero;
         }
+        // the tiles were written through the generic proxy; the tensor core reads them
+        // through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int kk = 0; kk < GK; kk += 16) {
-            uint32_t a[4];
-            const int ar = warp * 16 + g;
-            a[0] = *(const uint32_t*)&As[ar][kk + 2 * t];
-            a[1] = *(const uint32_t*)&As[ar + 8][kk + 2 * t];
-            a[2] = *(const uint32_t*)&As[ar][kk + 2 * t + 8];
-            a[3] = *(const uint32_t*)&As[ar + 8][kk + 2 * t + 8];
+            for (int kk = 0; kk < TK; kk += 16) {
+                const uint64_t ad = smem_desc(smem_u32(As) + (kk / 8) * 128, 128, (TK / 8) * 128);
+                const uint64_t bd = smem_desc(smem_u32(Bs) + (kk / 8) * 128, 128, (TK / 8) * 128);
+                const uint32_t acc_in = (k0 > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                    ::"r"(tmem), "l"(ad), "l"(bd), "r"(GEMM_IDESC), "r"(acc_in) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(mbar_a) : "memory");
+        }
+        issued = true;
+        // every thread waits until the MMAs have consumed the tiles (bounded)
+        uint32_t done = 0;
+        for (long long spins = 0; spins < GEMM_WAIT_SPINS; spins++) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done) : "r"(mbar_a), "r"(phase) : "memory");
+            if (done) break;
+        }
+        if (!done) s_fail = 1;
+        phase ^= 1u;
+        __syncthreads();
+        if (s_fail) break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!s_fail) {
+        const int row = m0 + warp * 32 + lane;
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-                uint32_t b[2];
-                b[0] = *(const uint32_t*)&Bs[j * 8 + g][kk + 2 * t];
-                b[1] = *(const uint32_t*)&Bs[j * 8 + g][kk + 2 * t + 8];
-                mma_bf16_16816(acc[j], a, b);
+        for (int c0 = 0; c0 < TN; c0 += 16) {
+            uint32_t r[16];
+            if (issued) {
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; q++) r[q] = 0u;
+            }
+            if (row < M) {
+#pragma unroll
+                for (int q = 0; q < 16; q++) {
+                    const int n = n0 + c0 + q;
+                    if (n < N) {
+                        float* c = C + (int64_t)row * scm + (int64_t)n * scn;
+                        *c = accumulate ? *c + __uint_as_float(r[q]) : __uint_as_float(r[q]);
+                    }
+                }
             }
         }
-        __syncthreads();
+    } else if (tid == 0) {
+        atomicExch(&g_gemm_err, 1u);
     }
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            int m = m0 + warp * 16 + g + (q >= 2 ? 8 : 0);
-            int n = n0 + j * 8 + 2 * t + (q & 1);
-            if (m < M && n < N) {
-                float* c = C + (int64_t)m * scm + (int64_t)n * scn;
-                *c = accumulate ? *c + acc[j][q] : acc[j][q];
-            }
-        }
-    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TN) : "memory");
 }
 
 static knn_status gemm(int M, int N, int K, const __nv_bfloat16* A, int64_t sam, int64_t sak, const __nv_bfloat16* B,
                        int64_t sbk, int64_t sbn, float* C, int64_t scm, int64_t scn, bool accumulate,
                        cudaStream_t stream) {
     if (M <= 0 || N <= 0) return KNN_OK;
-    dim3 grid((unsigned)ceil_div(N, GN), (unsigned)ceil_div(M, GM));
+    dim3 grid((unsigned)ceil_div(N, TN), (unsigned)ceil_div(M, TM));
     k_gemm_bf16<<<grid, 128, 0, stream>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, scm, scn, accumulate ? 1 : 0);
     KNN_CUDA_TRY(cudaGetLastError());
     count_launch();
+    return KNN_OK;
+}
+
+// Reports (and clears) a GEMM that gave up its bounded wait since the last check; the
+// caller has synchronised the stream.
+static knn_status gemm_check() {
+    unsigned e = 0;
+    KNN_CUDA_TRY(cudaMemcpyFromSymbol(&e, g_gemm_err, sizeof(e)));
+    if (e) {
+        const unsigned z = 0;
+        KNN_CUDA_TRY(cudaMemcpyToSymbol(g_gemm_err, &z, sizeof(z)));
+        return fail(KNN_ETIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs");
+    }
     return KNN_OK;
 }
 
@@ -415,6 +500,8 @@ static knn_status sketch(const DevCSR& r, uint32_t seed, __nv_bfloat16* X, cudaS
 
 float model_tau_scale(const knn_model* md) { return md->tau_scale; }
 
+knn_status model_check() { return gemm_check(); }
+
 // predicted k-th scores for every row of r (device float[n_rows]) in chunks
 knn_status model_predict_tau(const knn_model* md, const DevCSR& r, float tau_scale, float* tau, cudaStream_t s,
                              Buffers& tmp) {
@@ -572,6 +659,7 @@ extern "C" knn_status knn_threshold_model_train(knn_model* md, const knn_csr* Q,
         float hl = 0.0f;
         KNN_CUDA_TRY(cudaMemcpyAsync(&hl, w.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
         KNN_CUDA_TRY(cudaStreamSynchronize(s));
+        KNN_TRY(gemm_check());
         last_loss = hl / (double)(nb * batch);
     }
     if (final_loss) *final_loss = (float)last_loss;
@@ -589,7 +677,7 @@ extern "C" knn_status knn_threshold_model_predict(const knn_model* md, const knn
     if (!out_tau) return fail(KNN_EINVAL, "out_tau is NULL");
     KNN_TRY(model_predict_tau(md, r, 1.0f, out_tau, s, tmp));
     KNN_CUDA_TRY(cudaStreamSynchronize(s));
-    return KNN_OK;
+    return gemm_check();
 }
 
 extern "C" knn_status knn_threshold_model_calibrate(knn_model* md, const knn_csr* Q, const float* kth_scores,
@@ -612,6 +700,7 @@ extern "C" knn_status knn_threshold_model_calibrate(knn_model* md, const knn_csr
     std::vector<float> h((size_t)q.n_rows);
     KNN_CUDA_TRY(cudaMemcpyAsync(h.data(), ratio, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, s));
     KNN_CUDA_TRY(cudaStreamSynchronize(s));
+    KNN_TRY(gemm_check());
     // A row falls back iff scale * tau > kth, i.e. scale > kth / tau.  The value at rank
     // floor(miss_rate * n) leaves at most that many rows of Q below it; it is stepped down
     // by a relative 1e-6 so that the rounding of scale * tau cannot lift the row at that
@@ -700,15 +789,17 @@ extern "C" knn_status knn_threshold_model_forward_backward(knn_model* md, const 
     if (out_grads)
         KNN_CUDA_TRY(cudaMemcpyAsync(out_grads, md->grad, sizeof(float) * N_PARAMS, cudaMemcpyDeviceToDevice, s));
     KNN_CUDA_TRY(cudaStreamSynchronize(s));
-    return KNN_OK;
+    return gemm_check();
 }
 
 extern "C" knn_status knn_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int64_t sam, int64_t sak,
                                     const void* B, int64_t sbk, int64_t sbn, float* C, int64_t scm, int64_t scn,
                                     int32_t accumulate, void* stream) {
     if (M < 0 || N < 0 || K < 0 || (M && N && (!A || !B || !C))) return fail(KNN_EINVAL, "bad GEMM arguments");
-    return gemm(M, N, K, (const __nv_bfloat16*)A, sam, sak, (const __nv_bfloat16*)B, sbk, sbn, C, scm, scn,
-                accumulate != 0, (cudaStream_t)stream);
+    KNN_TRY(gemm(M, N, K, (const __nv_bfloat16*)A, sam, sak, (const __nv_bfloat16*)B, sbk, sbn, C, scm, scn,
+                 accumulate != 0, (cudaStream_t)stream));
+    KNN_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return gemm_check();
 }
 
 extern "C" knn_status knn_threshold_sketch(const knn_model* md, const knn_csr* R, void* out_x_bf16, void* stream_) {
