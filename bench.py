@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--batch-jobs", type=int, default=64)
     ap.add_argument("--no-bf", action="store_true", help="skip the brute-force comparison")
     ap.add_argument("--no-float", action="store_true", help="skip the float scale-up leg")
+    ap.add_argument("--mlp-gemm", action="store_true",
+                    help="only time the learned threshold's tensor-core GEMM (8192 x 256 x 528) and exit")
     ap.add_argument("--float-s", type=int, default=500000, help="|S| of the float scale-up leg")
     ap.add_argument("--float-r", type=int, default=10000, help="|R| of the float scale-up leg")
     ap.add_argument("--bf-rows", type=int, default=5000, help="R rows of the brute-force comparison")
@@ -602,9 +604,40 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def mlp_gemm(args):
+    """The learned threshold's first-layer GEMM shape for 8,192 queries, C = A B^T with
+    A [8192 x 528], B [256 x 528] in bf16, on the tcgen05 kernel: 3 warm-up calls, then
+    CUDA events around 20 calls; checked against an fp32 matmul of the same inputs."""
+    import torch
+    from paper_1011_2807_gb300.binding import knn_gemm_bf16
+    M, N, K = 8192, 256, 528
+    g = torch.Generator().manual_seed(0)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    C = torch.zeros(M, N, device="cuda")
+    call = lambda: knn_gemm_bf16(A, (K, 1), B, (1, K), C, (N, 1), M, N, K)
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 20
+    ref = A.float() @ B.float().t()
+    err = float((C - ref).abs().max() / ref.abs().max())
+    print(json.dumps({"kernel": "k_gemm_bf16 (tcgen05)", "M": M, "N": N, "K": K, "ms": ms,
+                      "tflops": 2 * M * N * K / ms / 1e9, "max_rel_err_vs_fp32": err}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.mlp_gemm:
+        mlp_gemm(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -158,16 +158,50 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const __
     const __nv_bfloat16 zero = __float2bfloat16(0.0f);
     uint32_t phase = 0;
     bool issued = false;
+    // With K contiguous (stride 1) and 16-byte aligned rows, 8 consecutive k of a row are
+    // one 16-byte row of a core matrix: staged with one 128-bit load and store.
+    const bool a_vec = sak == 1 && (sam & 7) == 0 && (((uintptr_t)A) & 15) == 0;
+    const bool b_vec = sbk == 1 && (sbn & 7) == 0 && (((uintptr_t)B) & 15) == 0;
     for (int k0 = 0; k0 < K; k0 += TK) {
-        for (int i = tid; i < TM * TK; i += 128) {
-            const int r = i / TK, c = i % TK;
-            const int m = m0 + r, k = k0 + c;
-            As[canon(r, c)] = (m < M && k < K) ? A[(int64_t)m * sam + (int64_t)k * sak] : zero;
+        if (a_vec) {
+            for (int i = tid; i < TM * (TK / 8); i += 128) {
+                const int r = i / (TK / 8), c = (i % (TK / 8)) * 8;
+                const int m = m0 + r, k = k0 + c;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (m < M && k + 8 <= K) {
+                    v = *(const uint4*)(A + (int64_t)m * sam + k);
+                } else if (m < M) {
+                    __nv_bfloat16* e = (__nv_bfloat16*)&v;
+                    for (int q = 0; q < 8 && k + q < K; q++) e[q] = A[(int64_t)m * sam + k + q];
+                }
+                *(uint4*)(As + canon(r, c)) = v;
+            }
+        } else {
+            for (int i = tid; i < TM * TK; i += 128) {
+                const int r = i / TK, c = i % TK;
+                const int m = m0 + r, k = k0 + c;
+                As[canon(r, c)] = (m < M && k < K) ? A[(int64_t)m * sam + (int64_t)k * sak] : zero;
+            }
         }
-        for (int i = tid; i < TN * TK; i += 128) {
-            const int r = i / TK, c = i % TK;   // r: n, c: k
-            const int n = n0 + r, k = k0 + c;
-            Bs[canon(r, c)] = (n < N && k < K) ? B[(int64_t)k * sbk + (int64_t)n * sbn] : zero;
+        if (b_vec) {
+            for (int i = tid; i < TN * (TK / 8); i += 128) {
+                const int r = i / (TK / 8), c = (i % (TK / 8)) * 8;   // r: n, c: k
+                const int n = n0 + r, k = k0 + c;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (n < N && k + 8 <= K) {
+                    v = *(const uint4*)(B + k + (int64_t)n * sbn);
+                } else if (n < N) {
+                    __nv_bfloat16* e = (__nv_bfloat16*)&v;
+                    for (int q = 0; q < 8 && k + q < K; q++) e[q] = B[k + q + (int64_t)n * sbn];
+                }
+                *(uint4*)(Bs + canon(r, c)) = v;
+            }
+        } else {
+            for (int i = tid; i < TN * TK; i += 128) {
+                const int r = i / TK, c = i % TK;   // r: n, c: k
+                const int n = n0 + r, k = k0 + c;
+                Bs[canon(r, c)] = (n < N && k < K) ? B[(int64_t)k * sbk + (int64_t)n * sbn] : zero;
+            }
         }
         // the tiles were written through the generic proxy; the tensor core reads them
         // through the async proxy
