@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-oracle sample time")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--n-train", type=int, default=20000, help="training queries of the learned threshold")
+    ap.add_argument("--n-train", type=int, default=200000, help="training queries of the learned threshold")
     ap.add_argument("--batch-jobs", type=int, default=64)
     ap.add_argument("--no-bf", action="store_true", help="skip the brute-force comparison")
     ap.add_argument("--no-float", action="store_true", help="skip the float scale-up leg")
@@ -417,7 +417,7 @@ def learned_leg(args, R, S, idx, Rd, ids, sc, plain_ms, reps):
     from paper_1011_2807_gb300 import synth
     k = args.k
     t0 = time.perf_counter()
-    n_val = max(1000, args.n_train // 4)
+    n_val = max(1000, min(10000, args.n_train // 4))
     A = synth.spectrum_u8(args.n_train + n_val, synth.config_seed(2, "train"), role="R")
     Ad = knn.DeviceCSR.from_host(A)
     _, asc = knn.knn_join(idx, Ad, k)
