@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--batch-jobs", type=int, default=64)
     ap.add_argument("--no-bf", action="store_true", help="skip the brute-force comparison")
     ap.add_argument("--no-float", action="store_true", help="skip the float scale-up leg")
+    ap.add_argument("--learned-full", action="store_true",
+                    help="only run the learned-threshold workload at full size (|S| = 5M, 200k training "
+                         "and 1M evaluation queries, k = 10) against the plain join, and exit")
     ap.add_argument("--mlp-gemm", action="store_true",
                     help="only time the learned threshold's tensor-core GEMM (8192 x 256 x 528) and exit")
     ap.add_argument("--float-s", type=int, default=500000, help="|S| of the float scale-up leg")
@@ -604,6 +607,45 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def learned_full(args):
+    """The learned-threshold workload at its stated size: |S| = 5,000,000 and 1,000,000
+    evaluation queries of the spectrum-shaped generator, k = 10; the model trains on
+    190,000 exact (query, k-th score) pairs and calibrates on 10,000 more (0.2 %
+    fallback target); plain and learned joins of the evaluation queries are timed with
+    CUDA events (1 warm-up, 2 timed) and their results compared."""
+    import torch
+    import paper_1011_2807_gb300 as knn
+    from paper_1011_2807_gb300 import synth
+    t0 = time.perf_counter()
+    T, E, S, k = synth.config4()
+    gen_s = time.perf_counter() - t0
+    idx = knn.knn_join_build_index(S)
+    Td, Ed = knn.DeviceCSR.from_host(T), knn.DeviceCSR.from_host(E)
+    _, tsc = knn.knn_join(idx, Td, k)
+    lab = tsc[:, k - 1].float()
+    n_fit = T.n_rows - 10000
+    model = knn.ThresholdModel(seed=1)
+    loss = model.train(T.slice_rows(0, n_fit), lab[:n_fit].contiguous(), epochs=15, batch=512, quantile=0.1, seed=1)
+    scale = model.calibrate(T.slice_rows(n_fit, T.n_rows), lab[n_fit:].contiguous(), 0.002)
+    pids, psc = knn.knn_join(idx, Ed, k)
+    torch.cuda.synchronize()
+    plain_ms = time_events(lambda: knn.knn_join(idx, Ed, k, skip_validation=True), 2)
+    res = {}
+    res["o"] = knn.knn_join_learned(idx, model, Ed, k)
+    torch.cuda.synchronize()
+    learned_ms = time_events(lambda: res.update(o=knn.knn_join_learned(idx, model, Ed, k)), 2)
+    lids, lsc, st = res["o"]
+    print(json.dumps({
+        "workload": f"learned threshold: |S|={S.n_rows:,}, {n_fit:,} training + 10,000 calibration queries, "
+                    f"{E.n_rows:,} evaluation queries, k={k}, spectrum-shaped uint8",
+        "plain_rows_per_s": E.n_rows / (plain_ms / 1e3), "learned_rows_per_s": E.n_rows / (learned_ms / 1e3),
+        "speedup": plain_ms / learned_ms, "identical": bool(torch.equal(pids, lids) and torch.equal(psc, lsc)),
+        "fallback_rate": st["fallback_rows"] / E.n_rows, "tau_scale": scale, "final_loss": loss,
+        "generate_s": gen_s}), flush=True)
+    model.close()
+    idx.close()
+
+
 def mlp_gemm(args):
     """The learned threshold's first-layer GEMM shape for 8,192 queries, C = A B^T with
     A [8192 x 528], B [256 x 528] in bf16, on the tcgen05 kernel: 3 warm-up calls, then
@@ -637,6 +679,8 @@ def main():
     args = parse()
     if args.mlp_gemm:
         mlp_gemm(args)
+    elif args.learned_full:
+        learned_full(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
