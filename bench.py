@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--block-size", type=int, default=0)
     ap.add_argument("--n-levels", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--blocks-per-launch", type=int, default=16, help="S blocks per k_join launch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-oracle sample time")
@@ -484,7 +485,8 @@ def run_ours(args):
     Rd = knn.DeviceCSR.from_host(R)
     ids = torch.empty((R.n_rows, k), dtype=torch.int32, device="cuda")
     sc = torch.empty((R.n_rows, k), dtype=torch.int32, device="cuda")
-    kw = dict(mode=args.mode, threads=args.threads, out_ids=ids, out_scores=sc)
+    kw = dict(mode=args.mode, threads=args.threads, blocks_per_launch=args.blocks_per_launch, out_ids=ids,
+              out_scores=sc)
     # validate R once, and count the postings one step scans
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     knn.knn_join(idx, Rd, k, postings_scanned=cnt, **kw)
@@ -552,14 +554,16 @@ def run_ours(args):
     alg_bytes = bytes_post + bytes_r + bytes_out
     kern_ms = statistics.mean(step_ms)
     achieved = alg_bytes / (kern_ms / 1000.0) / 1e9   # = bytes per launch / mean launch time
-    launches_per_step = max(1, launches // max(1, args.steps))
+    launches_per_step = max(1, launches // max(1, args.steps))   # k_join launches + R's row statistics
+    join_launches = -(-info["n_blocks"] // max(1, args.blocks_per_launch))
     traffic, traffic_note = profiled_traffic(os.path.join(ROOT, "paper_1011_2807_gb300", "csrc", "join.cu"))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_join (posting scan + accumulate + select + top-k, fused)",
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_step": alg_bytes, "kernel_launches_per_step": launches_per_step,
-                "algorithmic_bytes_per_launch": alg_bytes / launches_per_step,
+                "k_join_launches_per_step": join_launches,
+                "algorithmic_bytes_per_launch": alg_bytes / join_launches,
                 "traffic_unit": "DRAM bytes read + written per k_join launch (ncu, full-size launch)",
                 "bytes_per_unit": "4 B per posting scanned + 5 B per R feature + 8 B per R row index + 8k B output",
                 "iib_equivalent_GBps": (4 * p_iib + bytes_r + bytes_out) / (kern_ms / 1000.0) / 1e9}
