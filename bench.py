@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--batch-jobs", type=int, default=64)
     ap.add_argument("--no-bf", action="store_true", help="skip the brute-force comparison")
     ap.add_argument("--no-float", action="store_true", help="skip the float scale-up leg")
+    ap.add_argument("--no-host-index", action="store_true", help="skip the host-resident index leg")
     ap.add_argument("--learned-full", action="store_true",
                     help="only run the learned-threshold workload at full size (|S| = 5M, 200k training "
                          "and 1M evaluation queries, k = 10) against the plain join, and exit")
@@ -334,6 +335,28 @@ def batched_leg(args, R, S, reps):
                         "S = leading rows of the benchmark S, R = windows of the benchmark R"}
 
 
+def host_index_leg(args, S, Rd, ids, sc, plain_ms, reps):
+    """The out-of-core form: a second index of the same S moved into pinned host memory
+    (Grace LPDDR on a GB300 node); the full benchmark R joined against it over the host
+    link, against the device-resident join's time and results."""
+    import torch
+    import paper_1011_2807_gb300 as knn
+    idx = knn.knn_join_build_index(S, block_size=args.block_size, n_levels=args.n_levels)
+    dev_bytes = idx.info()["device_bytes"]
+    t0 = time.perf_counter()
+    idx.to_host()
+    move_s = time.perf_counter() - t0
+    kw = dict(mode=args.mode, threads=args.threads, blocks_per_launch=args.blocks_per_launch, skip_validation=True)
+    hids, hsc = knn.knn_join(idx, Rd, args.k, **kw)
+    torch.cuda.synchronize()
+    host_ms = time_events(lambda: knn.knn_join(idx, Rd, args.k, **kw), reps)
+    out = {"rows_per_s": Rd.n_rows / (host_ms / 1e3), "device_index_rows_per_s": Rd.n_rows / (plain_ms / 1e3),
+           "ratio_to_device_index": plain_ms / host_ms, "identical": bool(torch.equal(hids, ids) and torch.equal(hsc, sc)),
+           "index_bytes_moved": dev_bytes, "move_s": move_s, "host_bytes": idx.info()["host_bytes"]}
+    idx.close()
+    return out
+
+
 def bf_leg(args, R, idx, reps):
     """Brute force (Algorithm 2 on the GPU: every s scored in full) against the plain join,
     on the first rows of the benchmark R; the paper compares IIB/IIIB with it."""
@@ -570,7 +593,9 @@ def run_ours(args):
     if traffic_note:
         roofline["traffic_note"] = traffic_note
 
-    batched = learned = bf = flt = None
+    batched = learned = bf = flt = host = None
+    if rank == 0 and world == 1 and not args.no_host_index:
+        host = host_index_leg(args, S, Rd, ids, sc, kern_ms, reps=3)
     if rank == 0 and world == 1 and not args.no_bf:
         bf = bf_leg(args, R, idx, reps=2)
     if rank == 0 and world == 1 and not args.no_learned:
@@ -604,7 +629,8 @@ def run_ours(args):
                            "parallelism": f"R rows split over {world} GPU(s), index replicated"},
                 "gpu_launches": launches, "roofline": roofline, "clocks": clk,
                 "e2e": e2e, "cpu_baseline": cpu, "learned_vs_plain": learned, "batched_vs_plain": batched,
-                "bf_vs_plain": bf, "float_scaleup": flt, "kernel_ms_per_step": kern_ms}
+                "bf_vs_plain": bf, "float_scaleup": flt, "host_resident_index": host,
+                "kernel_ms_per_step": kern_ms}
         print(json.dumps(line), flush=True)
     idx.close()
     if world > 1:

@@ -113,6 +113,7 @@ typedef struct {
     knn_dtype dtype;
     int32_t max_row_nnz;
     size_t device_bytes;  /* bytes the index holds on the device */
+    size_t host_bytes;    /* bytes it holds in pinned host memory (knn_index_to_host) */
 } knn_index_info;
 
 /* Builds the index of S on the current device.
@@ -130,7 +131,21 @@ knn_status knn_join_build_index(const knn_csr* S, const knn_build_opts* opts, vo
 
 knn_status knn_index_get_info(const knn_index* index, knn_index_info* info);
 
-/* Frees the index (its device buffers go back to the allocator on its build stream). */
+/* Out-of-core form of Algorithm 1's block nested loop: moves every array of the index
+ * into pinned, mapped host memory (on a GB300 node, the Grace CPU's memory) and frees
+ * its device memory.  knn_join (and knn_join_learned) then stream the index: before
+ * each S-block-synchronous launch, that launch's slice (its S blocks' bins and
+ * postings, and the per-vector arrays of its S range) is copied into one of two
+ * device staging buffers on a copy stream while the previous launch runs; the staging
+ * memory (two slices) comes from the allocator for the duration of the call.  The
+ * batched form and knn_join_noalloc read the arrays in place over the host link
+ * (same results, much slower).  The build still needs device memory for the whole
+ * index.  Synchronises `stream` (NULL: the build stream).  A second call does nothing.
+ * Errors: KNN_ENOMEM (host allocation; the index is left unchanged), KNN_ECUDA.      */
+knn_status knn_index_to_host(knn_index* index, void* stream);
+
+/* Frees the index (device buffers go back to the allocator on its build stream, host
+ * arrays are released). */
 void knn_index_destroy(knn_index* index);
 
 /* ------------------------------------------------------------------------------ */
@@ -159,7 +174,7 @@ typedef struct {
                                    synchronises `stream` before returning                */
     int32_t skip_validation;    /* 1: trust R (sorted, in range, w > 0)                   */
     float level_margin;         /* Section 4.4 cut per S block: the highest level l with
-                                   M * L_l <= level_margin * theta (0 = 0.4).  Lower values
+                                   M * L_l <= level_margin * theta (0 = 0.3).  Lower values
                                    scan more postings and complete fewer candidates.     */
     int64_t* stats;             /* device int64[KNN_STATS_LEN] or NULL: work counters,
                                    added to (see KNN_STAT_*)                              */
@@ -212,7 +227,7 @@ typedef struct {
     int32_t threads;            /* threads per CTA for every job, power of two; 0 = 512.
                                    Every job's S block must lie in [4*threads, 64*threads]. */
     int32_t blocks_per_group;   /* S blocks per work item; 0 = 16                            */
-    float level_margin;         /* as in knn_join_opts (0 = 0.4)                             */
+    float level_margin;         /* as in knn_join_opts (0 = 0.3)                             */
     int32_t use_graph;          /* knn_batch_create: capture the launch into a CUDA graph   */
     int32_t skip_validation;    /* 1: trust every R                                          */
     int64_t* stats;             /* device int64[KNN_STATS_LEN] or NULL (all jobs together)   */

@@ -22,8 +22,8 @@ import numpy as np
 
 _lock = threading.Lock()
 
-DEFAULT = {"block_size": 16384, "threads": 512, "blocks_per_launch": 16, "level_margin": 0.4}
-MARGINS = (0.25, 0.4, 0.55)
+DEFAULT = {"block_size": 16384, "threads": 512, "blocks_per_launch": 16, "level_margin": 0.3}
+MARGINS = (0.25, 0.35, 0.45)
 
 
 def cache_path() -> str:

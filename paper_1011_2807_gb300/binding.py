@@ -54,7 +54,8 @@ class _IndexInfo(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int64), ("nnz", ctypes.c_int64), ("dim", ctypes.c_int32),
                 ("block_size", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
                 ("n_levels", ctypes.c_int32), ("dtype", ctypes.c_int),
-                ("max_row_nnz", ctypes.c_int32), ("device_bytes", ctypes.c_size_t)]
+                ("max_row_nnz", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
+                ("host_bytes", ctypes.c_size_t)]
 
 
 class _JoinOpts(ctypes.Structure):
@@ -111,6 +112,7 @@ def lib():
         L.knn_index_get_info.argtypes = [ctypes.c_void_p, P(_IndexInfo)]
         L.knn_index_destroy.argtypes = [ctypes.c_void_p]
         L.knn_index_destroy.restype = None
+        L.knn_index_to_host.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.knn_join.argtypes = [ctypes.c_void_p, P(_Csr), ctypes.c_int32, P(_JoinOpts),
                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.knn_join_noalloc.argtypes = [ctypes.c_void_p, P(_Csr), ctypes.c_int32, P(_JoinOpts),
@@ -221,6 +223,12 @@ class Index:
         if not self._h:
             raise ValueError("index is closed")
         return self._h
+
+    def to_host(self, stream=None) -> "Index":
+        """Moves the index into pinned host memory (knn_index_to_host); returns self."""
+        L = lib()
+        _check(L, L.knn_index_to_host(self.handle, _stream_ptr(stream) if stream is not None else None))
+        return self
 
     def info(self) -> dict:
         inf = _IndexInfo()

@@ -125,6 +125,9 @@ struct knn_index {
     uint32_t* ubound = nullptr;  // [n_levels * n_rows] weight sum of that prefix (u32 or f32 bits)
     cudaStream_t stream = nullptr;
     knn::Buffers* bufs = nullptr;
+    // after knn_index_to_host: the arrays above live in pinned, mapped host memory
+    std::vector<void*> host_arrays;
+    size_t host_bytes = 0;
 };
 
 namespace knn {

@@ -434,6 +434,60 @@ extern "C" knn_status knn_index_get_info(const knn_index* ix, knn_index_info* in
     info->dtype = ix->dtype;
     info->max_row_nnz = ix->max_row_nnz;
     info->device_bytes = ix->bufs ? ix->bufs->total() : 0;
+    info->host_bytes = ix->host_bytes;
+    return KNN_OK;
+}
+
+extern "C" knn_status knn_index_to_host(knn_index* ix, void* stream_) {
+    if (!ix) return fail(KNN_EINVAL, "NULL argument");
+    if (ix->host_bytes) return KNN_OK;
+    cudaStream_t s = stream_ ? (cudaStream_t)stream_ : ix->stream;
+    const size_t psz = ix->dtype == KNN_U8 ? 4 : 8, wsz = ix->dtype == KNN_U8 ? 1 : 4;
+    const size_t nbins = (size_t)ix->n_blocks * (size_t)ix->dim * (size_t)ix->n_levels;
+    struct Arr {
+        void** ptr;
+        size_t bytes;
+    } arrs[] = {
+        {(void**)&ix->binoff, (nbins + 1) * 4},
+        {&ix->postings, (size_t)ix->n_postings * psz},
+        {(void**)&ix->s_indptr, ((size_t)ix->n_rows + 1) * 8},
+        {(void**)&ix->sp_d, (size_t)ix->nnz * 4},
+        {&ix->sp_w, (size_t)ix->nnz * wsz},
+        {(void**)&ix->n_unidx, (size_t)ix->n_levels * (size_t)ix->n_rows * 2},
+        {(void**)&ix->ubound, (size_t)ix->n_levels * (size_t)ix->n_rows * 4},
+    };
+    std::vector<void*> host(7, nullptr);
+    auto undo = [&](knn_status st) {
+        for (void* h : host)
+            if (h) cudaFreeHost(h);
+        return st;
+    };
+    size_t total = 0;
+    for (int i = 0; i < 7; i++) {
+        const size_t bytes = arrs[i].bytes ? arrs[i].bytes : 16;
+        if (cudaHostAlloc(&host[i], bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            host[i] = nullptr;
+            return undo(fail(KNN_ENOMEM, "pinned host allocation of %zu bytes failed", bytes));
+        }
+        total += bytes;
+        if (arrs[i].bytes) {
+            cudaError_t e = cudaMemcpyAsync(host[i], *arrs[i].ptr, arrs[i].bytes, cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return undo(fail(KNN_ECUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e)));
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return undo(fail(KNN_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e)));
+    // the device addresses of the mapped host arrays (equal to the host addresses with
+    // unified addressing); from now on the joins read the index over the host link
+    std::vector<void*> dev(7, nullptr);
+    for (int i = 0; i < 7; i++) {
+        e = cudaHostGetDevicePointer(&dev[i], host[i], 0);
+        if (e != cudaSuccess) return undo(fail(KNN_ECUDA, "cudaHostGetDevicePointer: %s", cudaGetErrorString(e)));
+    }
+    for (int i = 0; i < 7; i++) *arrs[i].ptr = dev[i];
+    ix->bufs->release();
+    ix->host_arrays = host;
+    ix->host_bytes = total;
     return KNN_OK;
 }
 
@@ -443,5 +497,7 @@ extern "C" void knn_index_destroy(knn_index* ix) {
         ix->bufs->release();
         delete ix->bufs;
     }
+    for (void* h : ix->host_arrays)
+        if (h) cudaFreeHost(h);
     delete ix;
 }

@@ -148,6 +148,7 @@ struct JoinParams {
     const void* sp_w;
     const uint16_t* n_unidx;
     const uint32_t* ubound;
+    int64_t u_stride;   // elements between levels of n_unidx / ubound (|S|, or a staged slice's)
     float levels[KNN_MAX_LEVELS];
     int32_t k, groups, blocks_per_group, iiib, max_r_nnz;
     int32_t bf;         // brute force: every s scored in full (Algorithm 2), no posting scan
@@ -462,10 +463,10 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                 bool ok = true;
                 if (lvl > 0) {
                     const double th = JT<W>::score_of_bits((uint32_t)((kth > fl ? kth : fl) >> 32));
-                    ok = JT<W>::exact_ok(v, Mr, p.ubound[(int64_t)lvl * p.n_s + gid], th);
+                    ok = JT<W>::exact_ok(v, Mr, p.ubound[(int64_t)lvl * p.u_stride + gid], th);
                     if (ok) {   // Algorithm 4's dot over the unindexed features
                         const int64_t j0 = p.s_indptr[gid];
-                        const int m = p.n_unidx[(int64_t)lvl * p.n_s + gid];
+                        const int m = p.n_unidx[(int64_t)lvl * p.u_stride + gid];
                         Acc res = (Acc)0;
                         for (int q = 0; q < m; q++) {
                             const int32_t d = p.sp_d[j0 + q];
@@ -803,7 +804,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                             sortbuf[atomicAdd(&st.cnt, 1)] = key;
                             n_push++;
                         }
-                    } else if (JT<W>::exact_ok(v, M, p.ubound[(int64_t)level * p.n_s + gid], th)) {
+                    } else if (JT<W>::exact_ok(v, M, p.ubound[(int64_t)level * p.u_stride + gid], th)) {
                         const int slot = atomicAdd(&st.qcnt, 1);
                         if (slot >= CQ_CAP) break;   // queue full: keep this entry for the next pass
                         cq_gid[slot] = (uint32_t)gid;
@@ -821,7 +822,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
             for (int e = warp; e < nq; e += nwarps) {
                 const int64_t gid = cq_gid[e];
                 const int64_t j0 = p.s_indptr[gid];
-                const int m = p.n_unidx[(int64_t)level * p.n_s + gid];
+                const int m = p.n_unidx[(int64_t)level * p.u_stride + gid];
                 Acc res = (Acc)0;
                 for (int q = lane; q < m; q += 32) {
                     const int32_t d = p.sp_d[j0 + q];
@@ -1023,6 +1024,122 @@ __global__ void k_merge_groups(const u64* __restrict__ part, int64_t n_rows, int
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Out-of-core joins.  An index moved to host memory (knn_index_to_host) is streamed
+// launch by launch: each S-block-synchronous launch's slice of the index -- its bins,
+// postings and the per-vector arrays of its S range -- is copied into one of two device
+// staging sets on a copy stream while the previous launch runs, so the kernels read it
+// from device memory and L2 as usual (Algorithm 1's block nested loop with the S blocks
+// fetched from the host).
+// ---------------------------------------------------------------------------------
+struct StagedIndex {
+    cudaStream_t copy = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
+    uint32_t* binoff[2] = {nullptr, nullptr};
+    uint8_t* post[2] = {nullptr, nullptr};
+    int64_t* sind[2] = {nullptr, nullptr};
+    int32_t* spd[2] = {nullptr, nullptr};
+    uint8_t* spw[2] = {nullptr, nullptr};
+    uint16_t* nun[2] = {nullptr, nullptr};
+    uint32_t* ub[2] = {nullptr, nullptr};
+    int64_t rows_cap = 0;   // S vectors per launch: the staged arrays' level stride
+    ~StagedIndex() {
+        for (int i = 0; i < 2; i++) {
+            if (copied[i]) cudaEventDestroy(copied[i]);
+            if (used[i]) cudaEventDestroy(used[i]);
+        }
+        if (copy) cudaStreamDestroy(copy);
+    }
+};
+
+struct SliceRange {
+    int64_t b0, b1, g0, g1, p0, p1, f0, f1;   // blocks, S vectors, postings, features
+};
+
+static SliceRange slice_of(const knn_index* ix, int li, int per_launch) {
+    SliceRange r;
+    r.b0 = (int64_t)li * per_launch;
+    r.b1 = std::min<int64_t>(ix->n_blocks, r.b0 + per_launch);
+    r.g0 = r.b0 << ix->block_shift;
+    r.g1 = std::min<int64_t>(ix->n_rows, r.b1 << ix->block_shift);
+    const uint32_t* bo = (const uint32_t*)ix->host_arrays[0];
+    const int64_t* si = (const int64_t*)ix->host_arrays[2];
+    const int64_t lists = (int64_t)ix->dim * ix->n_levels;
+    r.p0 = bo[r.b0 * lists];
+    r.p1 = bo[r.b1 * lists];
+    r.f0 = si[r.g0];
+    r.f1 = si[r.g1];
+    return r;
+}
+
+static knn_status stage_setup(const knn_index* ix, int per_launch, int n_launch, Buffers& tmp, StagedIndex& st) {
+    const size_t psz = ix->dtype == KNN_U8 ? 4 : 8, wsz = ix->dtype == KNN_U8 ? 1 : 4;
+    int64_t post_cap = 1, feat_cap = 1;
+    for (int li = 0; li < n_launch; li++) {
+        const SliceRange r = slice_of(ix, li, per_launch);
+        post_cap = std::max(post_cap, r.p1 - r.p0);
+        feat_cap = std::max(feat_cap, r.f1 - r.f0);
+    }
+    st.rows_cap = (int64_t)per_launch << ix->block_shift;
+    const size_t bins = (size_t)per_launch * ix->dim * ix->n_levels + 1;
+    for (int i = 0; i < 2; i++) {
+        KNN_TRY(tmp.get(&st.binoff[i], bins));
+        KNN_TRY(tmp.get(&st.post[i], (size_t)post_cap * psz));
+        KNN_TRY(tmp.get(&st.sind[i], (size_t)st.rows_cap + 1));
+        KNN_TRY(tmp.get(&st.spd[i], (size_t)feat_cap));
+        KNN_TRY(tmp.get(&st.spw[i], (size_t)feat_cap * wsz));
+        KNN_TRY(tmp.get(&st.nun[i], (size_t)st.rows_cap * ix->n_levels));
+        KNN_TRY(tmp.get(&st.ub[i], (size_t)st.rows_cap * ix->n_levels));
+        KNN_CUDA_TRY(cudaEventCreateWithFlags(&st.copied[i], cudaEventDisableTiming));
+        KNN_CUDA_TRY(cudaEventCreateWithFlags(&st.used[i], cudaEventDisableTiming));
+    }
+    KNN_CUDA_TRY(cudaStreamCreateWithFlags(&st.copy, cudaStreamNonBlocking));
+    return KNN_OK;
+}
+
+// copies launch li's slice into set li & 1 (after the launch that last used that set)
+static knn_status stage_copy(const knn_index* ix, int li, int per_launch, bool wait_used, StagedIndex& st) {
+    const int set = li & 1;
+    const size_t psz = ix->dtype == KNN_U8 ? 4 : 8, wsz = ix->dtype == KNN_U8 ? 1 : 4;
+    const SliceRange r = slice_of(ix, li, per_launch);
+    const int64_t lists = (int64_t)ix->dim * ix->n_levels;
+    const int64_t rows = r.g1 - r.g0;
+    if (wait_used) KNN_CUDA_TRY(cudaStreamWaitEvent(st.copy, st.used[set], 0));
+    const uint8_t* const* h = (const uint8_t* const*)ix->host_arrays.data();
+    KNN_CUDA_TRY(cudaMemcpyAsync(st.binoff[set], h[0] + 4 * r.b0 * lists, 4 * ((r.b1 - r.b0) * lists + 1),
+                                 cudaMemcpyHostToDevice, st.copy));
+    KNN_CUDA_TRY(cudaMemcpyAsync(st.post[set], h[1] + psz * r.p0, psz * (r.p1 - r.p0), cudaMemcpyHostToDevice,
+                                 st.copy));
+    KNN_CUDA_TRY(cudaMemcpyAsync(st.sind[set], h[2] + 8 * r.g0, 8 * (rows + 1), cudaMemcpyHostToDevice, st.copy));
+    KNN_CUDA_TRY(cudaMemcpyAsync(st.spd[set], h[3] + 4 * r.f0, 4 * (r.f1 - r.f0), cudaMemcpyHostToDevice, st.copy));
+    KNN_CUDA_TRY(cudaMemcpyAsync(st.spw[set], h[4] + wsz * r.f0, wsz * (r.f1 - r.f0), cudaMemcpyHostToDevice,
+                                 st.copy));
+    // per level: the S range's entries, packed at a stride of rows_cap
+    KNN_CUDA_TRY(cudaMemcpy2DAsync(st.nun[set], 2 * st.rows_cap, h[5] + 2 * r.g0, 2 * ix->n_rows, 2 * rows,
+                                   ix->n_levels, cudaMemcpyHostToDevice, st.copy));
+    KNN_CUDA_TRY(cudaMemcpy2DAsync(st.ub[set], 4 * st.rows_cap, h[6] + 4 * r.g0, 4 * ix->n_rows, 4 * rows,
+                                   ix->n_levels, cudaMemcpyHostToDevice, st.copy));
+    KNN_CUDA_TRY(cudaEventRecord(st.copied[set], st.copy));
+    return KNN_OK;
+}
+
+// points the join's index arrays at launch li's staged slice (absolute indices still
+// work: every pointer is shifted back by the slice's first index)
+static void stage_params(const knn_index* ix, int li, int per_launch, const StagedIndex& st, JoinParams& p) {
+    const int set = li & 1;
+    const size_t psz = ix->dtype == KNN_U8 ? 4 : 8, wsz = ix->dtype == KNN_U8 ? 1 : 4;
+    const SliceRange r = slice_of(ix, li, per_launch);
+    const int64_t lists = (int64_t)ix->dim * ix->n_levels;
+    p.binoff = st.binoff[set] - r.b0 * lists;
+    p.postings = st.post[set] - psz * r.p0;
+    p.s_indptr = st.sind[set] - r.g0;
+    p.sp_d = st.spd[set] - r.f0;
+    p.sp_w = st.spw[set] - wsz * r.f0;
+    p.n_unidx = st.nun[set] - r.g0;
+    p.ubound = st.ub[set] - r.g0;
+    p.u_stride = st.rows_cap;
+}
+
 }  // namespace knn
 
 using namespace knn;
@@ -1087,6 +1204,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     }
     groups = std::max(1, std::min(groups, ix->n_blocks));
     groups = std::min(groups, std::max(1, 4096 / k));
+    if (ix->host_bytes) groups = 1;   // a host-resident index is streamed launch by launch
     int bpg = (int)ceil_div(ix->n_blocks, groups);
     groups = (int)ceil_div(ix->n_blocks, bpg);
     if ((int64_t)r.n_rows * groups > (int64_t)INT32_MAX) return fail(KNN_EUNSUPPORTED, "too many rows");
@@ -1115,6 +1233,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     p.sp_w = ix->sp_w;
     p.n_unidx = ix->n_unidx;
     p.ubound = ix->ubound;
+    p.u_stride = ix->n_rows;
     memcpy(p.levels, ix->levels, sizeof(p.levels));
     p.k = k;
     p.groups = groups;
@@ -1129,7 +1248,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     p.n_found = o.n_found;
     p.touched = (unsigned long long*)o.postings_scanned;
     p.stats = (unsigned long long*)o.stats;
-    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 0.4f;
+    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 0.3f;
     if (!(p.level_margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     if (groups > 1) {
         KNN_TRY(tmp.get(&p.part_keys, (size_t)r.n_rows * groups * k));
@@ -1145,14 +1264,27 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     per_launch = std::min(per_launch, ix->n_blocks);
     const int n_launch = groups == 1 ? (int)ceil_div(ix->n_blocks, per_launch) : 1;
     if (n_launch > 1) KNN_TRY(tmp.get(&p.carry, (size_t)r.n_rows * k));
+    StagedIndex staged;
+    const bool streamed = ix->host_bytes != 0;
+    if (streamed) {
+        KNN_TRY(stage_setup(ix, per_launch, n_launch, tmp, staged));
+        KNN_TRY(stage_copy(ix, 0, per_launch, false, staged));
+    }
     for (int li = 0; li < n_launch; li++) {
         p.block_begin = li * per_launch;
         p.block_end = std::min(ix->n_blocks, (li + 1) * per_launch);
         p.carry_in = li > 0;
         p.carry_out = li + 1 < n_launch;
+        if (streamed) {
+            // the next slice goes into the other set once the launch before this one is done
+            if (li + 1 < n_launch) KNN_TRY(stage_copy(ix, li + 1, per_launch, li >= 1, staged));
+            KNN_CUDA_TRY(cudaStreamWaitEvent(stream, staged.copied[li & 1], 0));
+            stage_params(ix, li, per_launch, staged, p);
+        }
         kern<<<(unsigned)grid, T, L.total, stream>>>(p);
         KNN_CUDA_TRY(cudaGetLastError());
         count_launch();
+        if (streamed) KNN_CUDA_TRY(cudaEventRecord(staged.used[li & 1], stream));
     }
     if (groups > 1) {
         int P = 2;
@@ -1291,6 +1423,7 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     p.sp_w = ix->sp_w;
     p.n_unidx = ix->n_unidx;
     p.ubound = ix->ubound;
+    p.u_stride = ix->n_rows;
     memcpy(p.levels, ix->levels, sizeof(p.levels));
     p.k = k;
     p.groups = 1;   // one group per row: the only schedule whose scratch is the carry buffer
@@ -1305,7 +1438,7 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     p.n_found = o.n_found;
     p.touched = (unsigned long long*)o.postings_scanned;
     p.stats = (unsigned long long*)o.stats;
-    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 0.4f;
+    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 0.3f;
     if (!(p.level_margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     p.carry = (u64*)((unsigned char*)scratch + NOALLOC_HEADER);
 
@@ -1390,7 +1523,7 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
     knn_batch_opts o = {};
     if (opts) o = *opts;
     if (o.mode != KNN_MODE_IIIB && o.mode != KNN_MODE_IIB) return fail(KNN_EINVAL, "unknown mode");
-    const float margin = o.level_margin > 0.0f ? o.level_margin : 0.4f;
+    const float margin = o.level_margin > 0.0f ? o.level_margin : 0.3f;
     if (!(margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     int dev = 0, smem_optin = 0, n_sm = 0;
     KNN_CUDA_TRY(cudaGetDevice(&dev));
@@ -1472,6 +1605,7 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
         p.sp_w = ix->sp_w;
         p.n_unidx = ix->n_unidx;
         p.ubound = ix->ubound;
+        p.u_stride = ix->n_rows;
         memcpy(p.levels, ix->levels, sizeof(p.levels));
         p.k = jb.k;
         p.groups = groups;

@@ -362,6 +362,37 @@ def test_bf_mode_reads_every_feature_of_s(knn):
 
 
 # ----------------------------------------------------------------------------------
+# the index in pinned host memory (out-of-core form): the same results
+# ----------------------------------------------------------------------------------
+
+def test_host_resident_index(knn, oracle_mod):
+    import torch
+    S = synth.spectrum_u8(20000, 161, role="S")
+    R = synth.spectrum_u8(150, 162, role="R")
+    Rd = knn.DeviceCSR.from_host(R)
+    idx = knn.knn_join_build_index(S, block_size=2048)
+    ref = {}
+    for mode, groups in (("iiib", 0), ("iiib", 3), ("iib", 1), ("bf", 1)):
+        ref[mode, groups] = knn.knn_join(idx, Rd, 7, mode=mode, s_groups=groups)
+    bref = knn.knn_join_batched([(idx, Rd, 7)])
+    before = idx.info()
+    assert before["device_bytes"] > 0 and before["host_bytes"] == 0
+    idx.to_host()
+    after = idx.info()
+    assert after["device_bytes"] == 0 and after["host_bytes"] >= before["device_bytes"] // 2
+    for (mode, groups), (ids, sc) in ref.items():
+        hids, hsc = knn.knn_join(idx, Rd, 7, mode=mode, s_groups=groups)
+        assert torch.equal(ids, hids) and torch.equal(sc, hsc), (mode, groups)
+    hb = knn.knn_join_batched([(idx, Rd, 7)])
+    assert torch.equal(bref[0][0], hb[0][0]) and torch.equal(bref[0][1], hb[0][1])
+    eids, esc, _ = oracle_mod.iib_join(R, S, 7, threads=8)
+    hids, hsc = knn.knn_join(idx, Rd, 7)
+    compare.assert_exact(hids.cpu().numpy(), hsc.cpu().numpy(), eids, esc, "host-resident index")
+    idx.to_host()   # a second move is a no-op
+    idx.close()
+
+
+# ----------------------------------------------------------------------------------
 # the benchmark's configuration at full size, on sampled rows
 # ----------------------------------------------------------------------------------
 
