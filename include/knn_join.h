@@ -182,6 +182,21 @@ typedef struct {
                                    every launch covers all rows (0 = 16)                   */
 } knn_join_opts;
 
+/* Top-k of the union of several S shards (no paper counterpart: the exchange step of
+ * an S-sharded join across GPUs, or of an S joined in ranges).  Part p holds, for the
+ * same n_rows queries, k entries per row as knn_join returns them (ids relative to the
+ * shard's first S vector, padding id -1 / score 0; device arrays); id_offset[p] (host)
+ * is that shard's first S id (0..2^31-1).  Writes the k best of all parts by (score
+ * desc, global id asc) with global ids, as knn_join would over the whole S; scores
+ * int32 (KNN_U8) or float32 (KNN_F32).  part_ids / part_scores / id_offset are host
+ * arrays of n_parts entries.  Asynchronous on `stream`.
+ * Errors: KNN_EINVAL (NULL, n_parts outside [1, KNN_MAX_PARTS], k outside
+ * [1, KNN_MAX_K], a bad offset).                                                      */
+#define KNN_MAX_PARTS 64
+knn_status knn_merge_topk(int32_t n_parts, const int32_t* const* part_ids, const void* const* part_scores,
+                          const int64_t* id_offset, int64_t n_rows, int32_t k, knn_dtype dtype,
+                          int32_t* out_ids, void* out_scores, void* stream);
+
 /* Work counters of knn_join (indices into knn_join_opts.stats). */
 #define KNN_STAT_BLOCK_STEPS 0      /* (row, S block) pairs processed                      */
 #define KNN_STAT_CANDIDATES 1       /* accumulator entries passing the level bound          */

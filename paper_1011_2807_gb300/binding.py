@@ -632,3 +632,33 @@ def knn_join_batched(jobs, *, mode="iiib", threads=0, blocks_per_group=0, level_
                    float(level_margin), 0, 0, None, 0, 0)
     _check(L, L.knn_join_batched(len(jobs), arr, ctypes.byref(o), _stream_ptr(stream)))
     return outs
+
+
+def knn_merge_topk(parts, offsets, k: int, stream=None):
+    """knn_merge_topk: parts = [(ids, scores), ...] (device [n_rows, k] tensors, as
+    knn_join returns them, ids relative to each shard), offsets = each shard's first S
+    id; returns the global (ids, scores) [n_rows, k]."""
+    L = lib()
+    if not getattr(L, "_merge_ready", False):
+        L.knn_merge_topk.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int64, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p]
+        L._merge_ready = True
+    n = len(parts)
+    if n != len(offsets):
+        raise ValueError("one offset per part")
+    ids0, sc0 = parts[0]
+    n_rows = ids0.shape[0]
+    for ids, sc in parts:
+        if ids.shape != (n_rows, k) or sc.shape != (n_rows, k) or not ids.is_cuda or not sc.is_cuda:
+            raise ValueError("every part must be a pair of device tensors [n_rows, k]")
+    dtype = KNN_F32 if sc0.dtype == torch.float32 else KNN_U8
+    parts = [(ids.contiguous(), sc.contiguous()) for ids, sc in parts]
+    pid = (ctypes.c_void_p * n)(*[ids.data_ptr() for ids, _ in parts])
+    psc = (ctypes.c_void_p * n)(*[sc.data_ptr() for _, sc in parts])
+    off = (ctypes.c_int64 * n)(*[int(o) for o in offsets])
+    out_ids = torch.empty((n_rows, k), dtype=torch.int32, device=ids0.device)
+    out_sc = torch.empty((n_rows, k), dtype=sc0.dtype, device=ids0.device)
+    _check(L, L.knn_merge_topk(n, pid, psc, off, int(n_rows), int(k), dtype, out_ids.data_ptr(), out_sc.data_ptr(),
+                               _stream_ptr(stream)))
+    return out_ids, out_sc

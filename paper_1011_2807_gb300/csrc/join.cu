@@ -1024,6 +1024,39 @@ __global__ void k_merge_groups(const u64* __restrict__ part, int64_t n_rows, int
     }
 }
 
+// Top-k of the union of several S shards' lists for the same queries: keys (score,
+// global id) from every part, a CTA bitonic sort per row, the first k kept.
+struct MergeParts {
+    const int32_t* ids[KNN_MAX_PARTS];
+    const uint32_t* scores[KNN_MAX_PARTS];   // int32 or float bits (both order like the scores)
+    int64_t offset[KNN_MAX_PARTS];           // the shard's first S id
+    int32_t n_parts;
+};
+static_assert(sizeof(MergeParts) < 4000, "merge parameters must fit the kernel parameter space");
+
+__global__ void k_merge_parts(const __grid_constant__ MergeParts mp, int k, int P, int32_t* __restrict__ out_ids,
+                              uint32_t* __restrict__ out_scores) {
+    extern __shared__ u64 buf[];
+    const int64_t row = blockIdx.x;
+    const int n = mp.n_parts * k;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        u64 key = 0ull;
+        if (i < n) {
+            const int part = i / k, q = i - part * k;
+            const int32_t id = mp.ids[part][row * k + q];
+            if (id >= 0) key = make_key(mp.scores[part][row * k + q], (uint32_t)(id + mp.offset[part]));
+        }
+        buf[i] = key;
+    }
+    __syncthreads();
+    cta_bitonic_desc(buf, P);
+    for (int q = threadIdx.x; q < k; q += blockDim.x) {
+        const u64 key = buf[q];
+        out_ids[row * k + q] = key ? (int32_t)key_gid(key) : -1;
+        out_scores[row * k + q] = key ? (uint32_t)(key >> 32) : 0u;
+    }
+}
+
 // ---------------------------------------------------------------------------------
 // Out-of-core joins.  An index moved to host memory (knn_index_to_host) is streamed
 // launch by launch: each S-block-synchronous launch's slice of the index -- its bins,
@@ -1300,6 +1333,36 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
         KNN_CUDA_TRY(cudaMemcpyAsync(out_scores, d_sc, sizeof(uint32_t) * r.n_rows * k, cudaMemcpyDeviceToHost, stream));
         KNN_CUDA_TRY(cudaStreamSynchronize(stream));
     }
+    return KNN_OK;
+}
+
+extern "C" knn_status knn_merge_topk(int32_t n_parts, const int32_t* const* part_ids, const void* const* part_scores,
+                                     const int64_t* id_offset, int64_t n_rows, int32_t k, knn_dtype dtype,
+                                     int32_t* out_ids, void* out_scores, void* stream_) {
+    if (n_parts < 1 || n_parts > KNN_MAX_PARTS) return fail(KNN_EINVAL, "n_parts must be in [1, %d]", KNN_MAX_PARTS);
+    if (k < 1 || k > KNN_MAX_K) return fail(KNN_EINVAL, "k must be in [1, %d]", KNN_MAX_K);
+    if (dtype != KNN_U8 && dtype != KNN_F32) return fail(KNN_EINVAL, "unknown dtype");
+    if (n_rows < 0) return fail(KNN_EINVAL, "n_rows < 0");
+    if (n_rows == 0) return KNN_OK;
+    if (!part_ids || !part_scores || !id_offset || !out_ids || !out_scores) return fail(KNN_EINVAL, "NULL argument");
+    MergeParts mp;
+    memset(&mp, 0, sizeof(mp));
+    mp.n_parts = n_parts;
+    for (int i = 0; i < n_parts; i++) {
+        if (!part_ids[i] || !part_scores[i]) return fail(KNN_EINVAL, "part %d is NULL", i);
+        if (id_offset[i] < 0 || id_offset[i] > 0x7FFFFFFF) return fail(KNN_EINVAL, "id offset of part %d", i);
+        mp.ids[i] = part_ids[i];
+        mp.scores[i] = (const uint32_t*)part_scores[i];
+        mp.offset[i] = id_offset[i];
+    }
+    if (n_rows > (int64_t)INT32_MAX) return fail(KNN_EUNSUPPORTED, "too many rows");
+    int P = 2;
+    while (P < n_parts * k) P <<= 1;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    KNN_CUDA_TRY(cudaFuncSetAttribute(k_merge_parts, cudaFuncAttributeMaxDynamicSharedMemorySize, P * 8));
+    k_merge_parts<<<(unsigned)n_rows, 256, (size_t)P * 8, stream>>>(mp, k, P, out_ids, (uint32_t*)out_scores);
+    KNN_CUDA_TRY(cudaGetLastError());
+    count_launch();
     return KNN_OK;
 }
 

@@ -393,6 +393,49 @@ def test_host_resident_index(knn, oracle_mod):
 
 
 # ----------------------------------------------------------------------------------
+# S in ranges (shards, or an S joined range by range) merged with knn_merge_topk
+# ----------------------------------------------------------------------------------
+
+def test_merge_topk_of_s_ranges(knn, oracle_mod):
+    import torch
+    from paper_1011_2807_gb300.binding import knn_merge_topk
+    S = synth.spectrum_u8(7000, 171, role="S")
+    R = synth.spectrum_u8(60, 172, role="R")
+    Rd = knn.DeviceCSR.from_host(R)
+    full = knn.knn_join_build_index(S, block_size=1024)
+    fids, fsc = knn.knn_join(full, Rd, 9)
+    cuts = [0, 2500, 2501, 7000]                 # a one-vector range in the middle
+    parts, idxs = [], []
+    for i, (a, b) in enumerate(zip(cuts[:-1], cuts[1:])):
+        idx = knn.knn_join_build_index(S.slice_rows(a, b), block_size=1024)
+        if i == 2:
+            idx.to_host()                          # one range joined from host memory
+        parts.append(knn.knn_join(idx, Rd, 9))
+        idxs.append(idx)
+    mids, msc = knn_merge_topk(parts, cuts[:-1], 9)
+    assert torch.equal(mids, fids) and torch.equal(msc, fsc)
+    eids, esc, _ = oracle_mod.iib_join(R, S, 9, threads=8)
+    compare.assert_exact(mids.cpu().numpy(), msc.cpu().numpy(), eids, esc, "merged ranges")
+    # float ranges
+    Sf = synth.zipf_f32(3000, 181, dim=2000, nnz_hi=200)
+    Rf = synth.zipf_f32(30, 182, dim=2000, nnz_hi=200)
+    Rfd = knn.DeviceCSR.from_host(Rf)
+    fparts = []
+    for a, b in ((0, 1700), (1700, 3000)):
+        idx = knn.knn_join_build_index(Sf.slice_rows(a, b), block_size=512)
+        fparts.append(knn.knn_join(idx, Rfd, 12))
+        idxs.append(idx)
+    fi, fs = knn_merge_topk(fparts, [0, 1700], 12)
+    eids, esc, _ = oracle_mod.iib_join(Rf, Sf, 12, threads=8)
+    compare.assert_close(Rf, Sf, list(range(Rf.n_rows)), fi.cpu().numpy(), fs.cpu().numpy(), eids, esc,
+                         what="merged float ranges")
+    with pytest.raises(ValueError):
+        knn_merge_topk(parts, [0, 1], 9)
+    for idx in idxs + [full]:
+        idx.close()
+
+
+# ----------------------------------------------------------------------------------
 # the benchmark's configuration at full size, on sampled rows
 # ----------------------------------------------------------------------------------
 

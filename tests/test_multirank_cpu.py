@@ -32,7 +32,7 @@ def _worker(rank, world, port, out):
 
 def test_two_ranks_on_gloo():
     port = 29500 + (os.getpid() % 1000)
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
