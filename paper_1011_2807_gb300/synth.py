@@ -19,9 +19,10 @@ in for both; their parameters are this library's own choice:
   sigma 200 bins, rounded and clipped), without replacement by rejection in draw
   order; w ~ U{1..100} as uint8.  Query rows draw nnz from a clipped log-normal
   (mean ~150, [20,600]); database rows from U{20..60}.
-* ``zipf_f32``: ids Zipf(alpha) over ranks mapped through a seeded permutation, nnz
-  from a discrete power law p(n) ~ n^-1.67 on [5, 2000], w log-normal(0,1), each row
-  L2-normalised.
+* ``zipf_f32``: ids Zipf(alpha) over ranks mapped through a seeded permutation (drawn
+  with Walker's alias method), without replacement by rejection in draw order; nnz
+  from a discrete power law p(n) ~ n^-1.67 on [5, 2000] (mean ~60), w log-normal(0,1),
+  each row L2-normalised.  Rows come in independently seeded chunks of 65,536.
 """
 from __future__ import annotations
 
@@ -157,29 +158,95 @@ def _unique_rows(rng, nnz, draw, dim, chunk=1 << 18, over=1.3, pos_bits=12):
     return indptr, out
 
 
-def _unique_rows_by_length(rng, nnz, draw, dim, budget=1 << 23):
-    """:func:`_unique_rows` for heavy-tailed row lengths: rows are visited in ascending
-    nnz order (stable), in chunks of about ``budget`` draws, so each chunk's oversampled
-    batch (2x) is sized by its own longest row.  Returns (indptr, indices) in the
-    original row order, each row's ids sorted ascending."""
-    n = int(nnz.shape[0])
-    nnz = nnz.astype(np.int64)
-    indptr = np.zeros(n + 1, dtype=np.int64)
-    np.cumsum(nnz, out=indptr[1:])
+def _first_distinct(rng, need, draw, width):
+    """First ``need[i]`` distinct ids of row i's own draw sequence, sorted ascending.
+
+    Every row gets ``width`` draws at once; rows that are still short extend their own
+    sequence by further batches (all short rows at once) until each holds its quota, so
+    each row is exactly the first distinct ids of one i.i.d. draw sequence.  Returns
+    (indptr, indices) in row order."""
+    m = int(need.shape[0])
+    need = need.astype(np.int64)
+    indptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(need, out=indptr[1:])
     out = np.empty(int(indptr[-1]), dtype=np.int32)
-    order = np.argsort(nnz, kind="stable")
-    a = 0
-    while a < n:
-        b = a + 1
-        while b < n and (b - a + 1) * (2 * int(nnz[order[b]]) + 8) <= budget:
-            b += 1
-        rows = order[a:b]
-        cptr, cidx = _unique_rows(rng, nnz[rows], draw, dim, chunk=b - a, over=2.0, pos_bits=13)
-        lens = nnz[rows]
-        dst = np.repeat(indptr[rows], lens) + (np.arange(int(lens.sum())) - np.repeat(cptr[:-1], lens))
-        out[dst] = cidx
-        a = b
+    rows = np.arange(m)
+    ids = draw(rng, (m, width))
+    while rows.size:
+        w = ids.shape[1]
+        pos_bits = max(1, int(w - 1).bit_length())
+        key = ids * (1 << pos_bits) + np.arange(w)[None, :]
+        key.sort(axis=1)
+        val = key >> pos_bits
+        first = np.ones(val.shape, dtype=bool)
+        first[:, 1:] = val[:, 1:] != val[:, :-1]
+        keep = np.zeros_like(first)
+        np.put_along_axis(keep, key & ((1 << pos_bits) - 1), first, axis=1)
+        cum = np.cumsum(keep, axis=1)
+        nd = need[rows]
+        ok = cum[:, -1] >= nd
+        if ok.any():
+            sel = keep[ok] & (cum[ok] <= nd[ok][:, None])
+            sval = np.where(sel, ids[ok], np.int64(1) << 40)
+            sval.sort(axis=1)
+            lens = nd[ok]
+            vals = sval[np.arange(w)[None, :] < lens[:, None]]
+            dst = np.repeat(indptr[rows[ok]], lens) + (np.arange(int(lens.sum()))
+                                                         - np.repeat(np.cumsum(lens) - lens, lens))
+            out[dst] = vals.astype(np.int32)
+        short = ~ok
+        rows = rows[short]
+        if rows.size:
+            ids = np.concatenate([ids[short], draw(rng, (int(rows.size), max(16, w // 4)))], axis=1)
     return indptr, out
+
+
+_ZIPF_TABLES: dict = {}
+
+
+def _zipf_tables(dim: int, alpha: float):
+    """Walker's alias table for p(rank) ~ rank^-alpha over ranks 1..dim (Vose's
+    construction), and, for every n <= dim, the number of i.i.d. draws whose expected
+    count of distinct ranks, sum_i 1 - (1 - p_i)^m, first reaches n."""
+    key = (dim, float(alpha))
+    if key in _ZIPF_TABLES:
+        return _ZIPF_TABLES[key]
+    p = np.arange(1, dim + 1, dtype=np.float64) ** (-alpha)
+    p /= p.sum()
+    scaled = p * dim
+    prob = np.ones(dim, dtype=np.float64)
+    alias = np.arange(dim, dtype=np.int64)
+    small = [i for i in range(dim) if scaled[i] < 1.0]
+    large = [i for i in range(dim) if scaled[i] >= 1.0]
+    while small and large:
+        s_, l_ = small.pop(), large.pop()
+        prob[s_] = scaled[s_]
+        alias[s_] = l_
+        scaled[l_] -= 1.0 - scaled[s_]
+        (small if scaled[l_] < 1.0 else large).append(l_)
+    # draws needed for n distinct: evaluate the expected distinct count on a grid of m
+    grid = np.unique(np.rint(np.geomspace(1, 64.0 * dim, 4096)).astype(np.int64))
+    q = np.log1p(-p)
+    expect = np.array([float((-np.expm1(m * q)).sum()) for m in grid])
+    n_all = np.arange(dim + 1, dtype=np.float64)
+    draws = grid[np.minimum(np.searchsorted(expect, n_all - 1e-6, side="left"), len(grid) - 1)]
+    _ZIPF_TABLES[key] = (prob, alias, draws)
+    return _ZIPF_TABLES[key]
+
+
+def _zipf_alias_draw(perm: np.ndarray, prob: np.ndarray, alias: np.ndarray):
+    dim = len(perm)
+
+    def draw(rng, shape):
+        x = rng.random(size=shape) * dim
+        i = x.astype(np.int64)
+        np.minimum(i, dim - 1, out=i)
+        r = np.where(x - i < prob[i], i, alias[i])
+        return perm[r]
+    return draw
+
+
+ZIPF_CHUNK = 1 << 16
 
 
 # ----------------------------------------------------------------------------------
@@ -202,21 +269,6 @@ def _mixture_draw(centres: np.ndarray, sigma: float, dim: int):
         comp = rng.integers(0, len(centres), size=shape)
         x = centres[comp] + sigma * rng.standard_normal(size=shape)
         return np.clip(np.rint(x), 0, dim - 1).astype(np.int64)
-    return draw
-
-
-def _zipf_draw(perm: np.ndarray, alpha: float):
-    dim = len(perm)
-    ranks = np.arange(1, dim + 1, dtype=np.float64)
-    p = ranks ** (-alpha)
-    cdf = np.cumsum(p)
-    cdf /= cdf[-1]
-
-    def draw(rng, shape):
-        u = rng.random(size=shape)
-        r = np.searchsorted(cdf, u, side="right")
-        r = np.minimum(r, dim - 1)
-        return perm[r].astype(np.int64)
     return draw
 
 
@@ -265,19 +317,89 @@ def powerlaw_nnz(rng, n: int, lo: int = 5, hi: int = 2000, a: float = 1.67) -> n
     return (lo + np.searchsorted(cdf, rng.random(size=n), side="right")).clip(lo, hi).astype(np.int64)
 
 
-def zipf_f32(n: int, seed: int, *, dim: int = 50000, alpha: float = 1.1,
-             perm_seed: int | None = None, nnz_lo: int = 5, nnz_hi: int = 2000) -> CSR:
-    """Zipf ids over a seeded permutation, power-law nnz, L2-normalised log-normal w."""
-    rng = np.random.default_rng(seed)
+def _zipf_chunk(n: int, seed: int, chunk: int, dim: int, alpha: float, perm: np.ndarray,
+                nnz_lo: int, nnz_hi: int, budget: int = 1 << 23):
+    """Rows of chunk ``chunk`` of a Zipf workload, from their own generator
+    (entropy [seed, chunk]): nnz, ids, log-normal w, L2-normalised.  Ids are drawn for
+    rows in ascending nnz order, in sub-chunks of at most ``budget`` draws whose rows'
+    draw widths lie within 1.25x of each other."""
+    rng = np.random.default_rng([seed, chunk])
     nnz = np.minimum(powerlaw_nnz(rng, n, nnz_lo, nnz_hi), dim)
-    perm = np.random.default_rng(config_seed(5, "mix") if perm_seed is None else perm_seed).permutation(dim)
-    indptr, idx = _unique_rows_by_length(rng, nnz, _zipf_draw(perm, alpha), dim)
+    prob, alias, draws = _zipf_tables(dim, alpha)
+    draw = _zipf_alias_draw(perm, prob, alias)
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(nnz, out=indptr[1:])
+    idx = np.empty(int(indptr[-1]), dtype=np.int32)
+    order = np.argsort(nnz, kind="stable")
+    width = (draws[nnz[order]] * 1.1).astype(np.int64) + 16      # ascending with the rows
+    a = 0
+    while a < n:
+        # rows whose draw width is within 1.25x of the first one's, up to ``budget`` draws
+        top = a + int(np.searchsorted(width[a:], int(width[a] * 1.25), side="right"))
+        cost = (np.arange(1, top - a + 1, dtype=np.int64)) * width[a:top]
+        b = a + max(1, int(np.searchsorted(cost, budget, side="right")))
+        rows = order[a:b]
+        lens = nnz[rows]
+        cptr, cidx = _first_distinct(rng, lens, draw, int(width[b - 1]))
+        dst = np.repeat(indptr[rows], lens) + (np.arange(int(lens.sum())) - np.repeat(cptr[:-1], lens))
+        idx[dst] = cidx
+        a = b
     w = rng.lognormal(0.0, 1.0, size=idx.shape[0])
-    rows = np.repeat(np.arange(n), np.diff(indptr))
-    norm = np.sqrt(np.bincount(rows, weights=w * w, minlength=n))
-    vals = (w / norm[rows]).astype(np.float32)
+    rid = np.repeat(np.arange(n), nnz)
+    norm = np.sqrt(np.bincount(rid, weights=w * w, minlength=n))
+    vals = (w / norm[rid]).astype(np.float32)
     vals = np.maximum(vals, np.float32(np.finfo(np.float32).tiny))
+    return nnz, idx, vals
+
+
+def zipf_f32(n: int, seed: int, *, dim: int = 50000, alpha: float = 1.1,
+             perm_seed: int | None = None, nnz_lo: int = 5, nnz_hi: int = 2000,
+             processes: int = 1) -> CSR:
+    """Zipf ids over a seeded permutation, power-law nnz, L2-normalised log-normal w.
+
+    Rows come in chunks of ``ZIPF_CHUNK`` rows, each drawn by its own generator, so the
+    first rows of a longer set equal a shorter set whose size is a multiple of the
+    chunk.  With ``processes`` > 1 the chunks are drawn by a pool of that many
+    processes (spawned, so it is safe after CUDA has been initialised); the result does
+    not depend on it."""
+    n_chunks = (n + ZIPF_CHUNK - 1) // ZIPF_CHUNK
+    args = [(n, seed, c, dim, alpha, perm_seed, nnz_lo, nnz_hi) for c in range(n_chunks)]
+    if processes > 1 and n_chunks > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(processes, n_chunks)) as pool:
+            chunks = pool.starmap(_zipf_chunk_args, args)
+    else:
+        chunks = [_zipf_chunk_args(*a) for a in args]
+    nnz = np.concatenate([c[0] for c in chunks]) if chunks else np.zeros(0, np.int64)
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(nnz, out=indptr[1:])
+    idx = np.concatenate([c[1] for c in chunks]) if chunks else np.zeros(0, np.int32)
+    vals = np.concatenate([c[2] for c in chunks]) if chunks else np.zeros(0, np.float32)
     return CSR(indptr, idx, vals, dim)
+
+
+def _zipf_chunk_args(n, seed, chunk, dim, alpha, perm_seed, nnz_lo, nnz_hi):
+    """Chunk ``chunk`` of ``zipf_f32(n, seed, ...)``: (nnz, indices, values)."""
+    perm = np.random.default_rng(config_seed(5, "mix") if perm_seed is None else perm_seed).permutation(dim)
+    rows = min(ZIPF_CHUNK, n - chunk * ZIPF_CHUNK)
+    return _zipf_chunk(rows, seed, chunk, dim, alpha, perm, nnz_lo, nnz_hi)
+
+
+def _call(name, args, kwargs):
+    return globals()[name](*args, **kwargs)
+
+
+def generate(calls, processes: int = 1):
+    """Run generator calls ``[(name, args, kwargs), ...]`` (names of this module's
+    functions) and return their results in order; with ``processes`` > 1, in a pool of
+    that many spawned processes.  Every generator is seeded by its arguments, so the
+    results do not depend on ``processes``."""
+    calls = [(c[0], tuple(c[1]), dict(c[2]) if len(c) > 2 else {}) for c in calls]
+    if processes > 1 and len(calls) > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(processes, len(calls))) as pool:
+            return pool.starmap(_call, calls)
+    return [_call(*c) for c in calls]
 
 
 # ----------------------------------------------------------------------------------
@@ -332,10 +454,10 @@ def config4(scale: float = 1.0, n_train: int | None = None, n_eval: int | None =
     return T, E, S, 10
 
 
-def config5(scale: float = 1.0, n_r: int | None = None, n_s: int | None = None):
+def config5(scale: float = 1.0, n_r: int | None = None, n_s: int | None = None, processes: int = 1):
     """Float scale-up: |R|=1M, |S|=10M, d=50,000, Zipf(1.1) ids, L2-normalised, k=20."""
     nr = n_r if n_r is not None else max(1, int(1000000 * scale))
     ns = n_s if n_s is not None else max(1, int(10000000 * scale))
-    S = zipf_f32(ns, config_seed(5, "S"))
-    R = zipf_f32(nr, config_seed(5, "R"))
+    S = zipf_f32(ns, config_seed(5, "S"), processes=processes)
+    R = zipf_f32(nr, config_seed(5, "R"), processes=processes)
     return R, S, 20
