@@ -70,13 +70,6 @@ struct JT<uint8_t> {
         return (u64)(uint32_t)c << 32;
     }
     static constexpr double SLACK = 0.0;
-    // Smallest score with which an s of the current S block can still enter: the k-th
-    // key came from earlier blocks, whose ids are all smaller, so a tie with its score
-    // loses; the floor (a caller threshold or another group's k-th key) admits ties.
-    __device__ static double entry_score(u64 kth, u64 fl) {
-        const double a = kth ? (double)(uint32_t)(kth >> 32) + 1.0 : 0.0;
-        return fmax(a, (double)(uint32_t)(fl >> 32));
-    }
     // bound on the unindexed residual at a level: M * (largest integer weight sum <= L)
     __device__ static double level_bound(double M, float L) { return M * floor((double)L); }
     // smallest partial score whose upper bound (partial + lb) reaches theta
@@ -93,6 +86,37 @@ struct JT<uint8_t> {
     __device__ static void set_cmin(S& st, int32_t c) { st.cmin_i = c; }
     template <class S>
     __device__ static int32_t get_cmin(const S& st) { return st.cmin_i; }
+    // Per-block threshold arithmetic in the score's own type (integers), so that the
+    // level choice of every block step needs no double-precision instructions.
+    using Th = uint32_t;   // int32 scores + 1 fit; a floor of 2^32 - 1 admits nothing
+    // Smallest score with which an s of the current S block can still enter: the k-th
+    // key came from earlier blocks, whose ids are all smaller, so a tie with its score
+    // loses; the floor (a caller threshold or another group's k-th key) admits ties.
+    __device__ static Th entry_th(u64 kth, u64 fl) {
+        const Th a = kth ? (uint32_t)(kth >> 32) + 1u : 0u;
+        return max(a, (uint32_t)(fl >> 32));
+    }
+    __device__ static double th_value(Th t) { return (double)t; }
+    // smallest integer theta with lb < theta (exact) and lb <= margin * theta (the margin
+    // only steers the work: its quotient uses the fast reciprocal, which keeps double
+    // division and its register cost out of the kernel); saturated at 2^32 - 1, as no
+    // int32 score reaches a theta that large
+    __device__ static Th level_need(double lb, float margin) {
+        const double n = fmax(floor(lb) + 1.0, ceil(lb * (double)__fdividef(1.0f, margin)));
+        return n < 4294967295.0 ? (Th)n : 0xFFFFFFFFu;
+    }
+    __device__ static Th bound_up(double lb) { return lb < 4294967295.0 ? (Th)ceil(lb) : 0xFFFFFFFFu; }
+    // cheap_min for an integer theta and the bound rounded up: max(1, theta - lbu)
+    __device__ static int32_t cheap_min_th(Th theta, Th lbu) {
+        const uint32_t c = theta > lbu ? theta - lbu : 1u;
+        return c > 2147483647u ? 2147483647 : (int32_t)max(c, 1u);
+    }
+    template <class S>
+    __device__ static Th& need(S& st, int l) { return st.need_i[l]; }
+    template <class S>
+    __device__ static Th& lbu(S& st, int l) { return st.lbu_i[l]; }
+    template <class S>
+    __device__ static Th& theta(S& st) { return st.theta_i; }
 };
 template <>
 struct JT<float> {
@@ -114,11 +138,6 @@ struct JT<float> {
     }
     // fp32 sums may differ from the real sum by a few ulps; widen bounds a little
     static constexpr double SLACK = 1.0 / (1 << 20);
-    // as for integers, with the next float above the k-th score (scores are finite and > 0)
-    __device__ static double entry_score(u64 kth, u64 fl) {
-        const double a = kth ? (double)__uint_as_float((uint32_t)(kth >> 32) + 1u) : 0.0;
-        return fmax(a, (double)__uint_as_float((uint32_t)(fl >> 32)));
-    }
     __device__ static double level_bound(double M, float L) { return M * (double)L * (1.0 + SLACK); }
     __device__ static float cheap_min(double theta, double lb) {
         double c = (theta - lb) * (1.0 - SLACK);
@@ -132,6 +151,33 @@ struct JT<float> {
     __device__ static void set_cmin(S& st, float c) { st.cmin_f = c; }
     template <class S>
     __device__ static float get_cmin(const S& st) { return st.cmin_f; }
+    // Per-block threshold arithmetic in float, rounded so that the level test and the
+    // candidate cut stay on the safe side of their double-precision definitions.
+    using Th = float;
+    // as for integers, with the next float above the k-th score (scores are finite and > 0)
+    __device__ static Th entry_th(u64 kth, u64 fl) {
+        const float a = kth ? __uint_as_float((uint32_t)(kth >> 32) + 1u) : 0.0f;
+        return fmaxf(a, __uint_as_float((uint32_t)(fl >> 32)));
+    }
+    __device__ static double th_value(Th t) { return (double)t; }
+    // smallest float theta with lb < theta (exact); the margin part as for integers
+    __device__ static Th level_need(double lb, float margin) {
+        float a = __double2float_ru(lb);   // >= lb >= 0; the next float if equal
+        if ((double)a <= lb && a < __int_as_float(0x7f800000)) a = __uint_as_float(__float_as_uint(a) + 1u);
+        return fmaxf(a, __double2float_ru(lb * (double)__fdividef(1.0f, margin)));
+    }
+    __device__ static Th bound_up(double lb) { return __double2float_ru(lb); }
+    // cheap_min from the bound rounded up, rounding down: at most its double value
+    __device__ static float cheap_min_th(Th theta, Th lbu) {
+        const float c = __fmul_rd(__fsub_rd(theta, lbu), 1.0f - 1.0f / 1048576.0f);   // 1 - SLACK
+        return fmaxf(c, 1.40129846e-45f);
+    }
+    template <class S>
+    __device__ static Th& need(S& st, int l) { return st.need_f[l]; }
+    template <class S>
+    __device__ static Th& lbu(S& st, int l) { return st.lbu_f[l]; }
+    template <class S>
+    __device__ static Th& theta(S& st) { return st.theta_f; }
 };
 
 struct JoinParams {
@@ -217,7 +263,8 @@ struct CtaState {
     int level;
     int pending[2]; // candidates still masked (overflow rounds), by S block parity: warp 0
                     // resets the next block's count while others may still read this one
-    double theta;   // pruning threshold of the current block
+    uint32_t theta_i;  // entry threshold of the current block (integer / float scores)
+    float theta_f;
     u64 floor;      // keys below this never qualify
     u64 kth;        // current k-th key (0 while fewer than k)
     double M;       // largest weight of r
@@ -225,6 +272,8 @@ struct CtaState {
     float cmin_f;   // smallest partial score worth a look in this block (as float/int)
     int32_t cmin_i;
     double lbnd[KNN_MAX_LEVELS];  // residual bound of every level for this row
+    uint32_t need_i[KNN_MAX_LEVELS], lbu_i[KNN_MAX_LEVELS]; // per level: smallest theta that
+    float need_f[KNN_MAX_LEVELS], lbu_f[KNN_MAX_LEVELS];    // may use it, bound rounded up
     unsigned long long n_steps, n_merges, n_rounds;  // work counters (thread 0)
     int qcnt;       // entries in the completion queue
     int dq_n;       // candidates deferred to warp 0 (in the completion queue's arrays)
@@ -370,7 +419,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     using Acc = typename JT<W>::Acc;
     using Post = typename JT<W>::Post;
     __shared__ CtaState st;
-    __shared__ double red_d[32];
+    __shared__ uint32_t red_m[32];
     __shared__ unsigned long long red_u[32];
 
     const int nb = 1 << p.block_shift;
@@ -394,15 +443,15 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     const int rn = (int)(p.r_indptr[row + 1] - ra);
 
     // load r (ascending d) and its largest weight
-    double mloc = 0.0;
+    uint32_t mloc = 0u;   // as score bits: weights are > 0, so the bits order like the values
     for (int i = tid; i < rn; i += T) {
         rf_d[i] = p.r_idx[ra + i];
         Acc w = (Acc)((const W*)p.r_val)[ra + i];
         rf_w[i] = w;
-        mloc = fmax(mloc, (double)w);
+        mloc = max(mloc, JT<W>::score_bits(w));
     }
-    for (int o = 16; o > 0; o >>= 1) mloc = fmax(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
-    if (lane == 0) red_d[warp] = mloc;
+    mloc = __reduce_max_sync(0xffffffffu, mloc);
+    if (lane == 0) red_m[warp] = mloc;
     // clear the accumulator (and the dense copy of r)
     for (int i = tid * 4; i < nb; i += T * 4) *(int4*)(acc + i) = make_int4(0, 0, 0, 0);
     if (rden) {
@@ -411,19 +460,26 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         for (int i = tid; i < rn; i += T) rden[rf_d[i]] = (uint8_t)rf_w[i];
     }
     __syncthreads();
-    if (tid == 0) {
-        double m = 0.0;
-        for (int w = 0; w < nwarps; w++) m = fmax(m, red_d[w]);
-        st.M = m;
-        st.size = 0;
-        st.cnt = 0;
-        st.kth = 0ull;
-        st.floor = p.init_thr ? JT<W>::floor_key(p.init_thr[row]) : ((u64)1 << 32);
-        st.n_steps = st.n_merges = st.n_rounds = 0;
-        st.qcnt = 0;
-        st.dq_n = 0;
-        st.pred_level = -1;
-        for (int l = 0; l < p.n_levels; l++) st.lbnd[l] = l ? JT<W>::level_bound(m, p.levels[l]) : 0.0;
+    if (warp == 0) {
+        const double m = (double)JT<W>::value_of_bits(
+            __reduce_max_sync(0xffffffffu, lane < nwarps ? red_m[lane] : 0u));
+        if (lane < p.n_levels) {   // lane l: level l's bound and the thresholds derived from it
+            const double lb = lane ? JT<W>::level_bound(m, p.levels[lane]) : 0.0;
+            st.lbnd[lane] = lb;
+            JT<W>::need(st, lane) = JT<W>::level_need(lb, p.level_margin);
+            JT<W>::lbu(st, lane) = JT<W>::bound_up(lb);
+        }
+        if (lane == 0) {
+            st.M = m;
+            st.size = 0;
+            st.cnt = 0;
+            st.kth = 0ull;
+            st.floor = p.init_thr ? JT<W>::floor_key(p.init_thr[row]) : ((u64)1 << 32);
+            st.n_steps = st.n_merges = st.n_rounds = 0;
+            st.qcnt = 0;
+            st.dq_n = 0;
+            st.pred_level = -1;
+        }
     }
     if (carry_in) {   // the row's top-k from the earlier S blocks
         for (int q = tid; q < p.k; q += T) topk[q] = __ldcg(p.carry + row * p.k + q);
@@ -528,23 +584,22 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                 u64 shared = *(volatile u64*)(p.floor_keys + row);
                 if (shared > fl) fl = shared;
             }
-            const double theta = JT<W>::entry_score(st.kth, fl);
+            // the highest level l with M * L_l < theta and M * L_l <= margin * theta,
+            // compared in the score's own type against thresholds set up per row
+            const auto theta = JT<W>::entry_th(st.kth, fl);
             bool ok = false;
-            if (p.iiib && lane >= 1 && lane < p.n_levels) {
-                const double lb = st.lbnd[lane];
-                ok = lb < theta && lb <= p.level_margin * theta;
-            }
+            if (p.iiib && lane >= 1 && lane < p.n_levels) ok = theta >= JT<W>::need(st, lane);
             const unsigned m = __ballot_sync(0xffffffffu, ok);
             const int level = m ? 31 - __clz(m) : 0;
             if (lane == 0) {
                 st.floor = fl;
-                st.theta = theta;
+                JT<W>::theta(st) = theta;
                 st.level = level;
                 st.need_prepare = !BF && st.pred_level != level;
                 st.pending[b & 1] = 0;
                 st.n_steps++;
                 st.lb = st.lbnd[level];
-                JT<W>::set_cmin(st, JT<W>::cheap_min(theta, st.lb));
+                JT<W>::set_cmin(st, JT<W>::cheap_min_th(theta, JT<W>::lbu(st, level)));
             }
         }
         __syncthreads();
@@ -786,8 +841,8 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         while (true) {
             const u64 kth = st.kth;
             const u64 fl = st.floor;
-            const double th = one_round ? st.theta
-                                        : fmax(st.theta, JT<W>::score_of_bits((uint32_t)((kth > fl ? kth : fl) >> 32)));
+            const double th0 = JT<W>::th_value(JT<W>::theta(st));
+            const double th = one_round ? th0 : fmax(th0, JT<W>::score_of_bits((uint32_t)((kth > fl ? kth : fl) >> 32)));
             const Acc cm = one_round ? cmin : JT<W>::cheap_min(th, lb);
             // (a) each thread takes its marked entries: level 0 pushes directly; above
             //     level 0, entries within the per-vector bound go to the completion queue

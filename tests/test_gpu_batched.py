@@ -126,7 +126,8 @@ def test_autotune_picks_a_valid_config(knn, tmp_path, monkeypatch):
     assert 4 * best["threads"] <= best["block_size"] <= 64 * best["threads"] and best["ms"] > 0
     got = autotune.lookup(S.n_rows, R.n_rows, R.nnz / R.n_rows, 5, "u8")
     assert got["block_size"] == best["block_size"]
-    assert got["level_margin"] in autotune.MARGINS
+    # the default margin stays unless one of the alternatives times faster
+    assert got["level_margin"] in (autotune.DEFAULT["level_margin"],) + autotune.MARGINS
 
 
 def test_bounded_wait_reports_timeout(knn, jobs):
