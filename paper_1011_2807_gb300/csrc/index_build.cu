@@ -198,10 +198,10 @@ __global__ void k_scatter(const int64_t* __restrict__ indptr, const int32_t* __r
     }
 }
 
-// Orders the postings of every bin inside each work item of its list (32 chunks, the
-// unit the join's scan hands to an 8-lane group) so that postings in the same slot j of
-// the item's chunks fall into different shared-memory banks (local id mod 32) wherever
-// the bin's contents allow: the 8 lanes of a group add slot j of 8 consecutive chunks
+// Orders the postings of every bin inside each 32-chunk window of its list (half of
+// the join's work item) so that postings in the same slot j of the window's chunks fall
+// into different shared-memory banks (local id mod 32) wherever the bin's contents
+// allow: the 16 lanes of a sub-warp add slot j of 16 consecutive chunks of one window
 // with one instruction.  Only the order inside a bin changes, so every level's prefix
 // keeps the same postings.  One thread per (S block, d) list.
 template <class Post, int V>

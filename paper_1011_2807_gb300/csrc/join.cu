@@ -280,6 +280,7 @@ struct CtaState {
     int dq_level;   // level of the block they came from
     int pred_level; // level the next block's list ranges were prepared for (-1: none)
     int need_prepare;
+    int allowed;    // highest level the current threshold allows (the next block's plan)
     // radix select of a candidate threshold (blocks with too many candidates)
     int rs_shift, rs_need, rs_done;
     unsigned rs_prefix, rs_above, rs_key;
@@ -574,7 +575,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         // previous block's scan, for the level that block used; they are prepared here,
         // by the whole CTA, only for a launch's first block or when the level changed.
         constexpr int V = JT<W>::PER_VEC;   // postings per 16-byte chunk
-        constexpr int G = 8, U = 4, CH = G * U;
+        constexpr int G = 16, U = 4, CH = G * U;
         uint32_t* lbeg = lbeg_buf + (b & 1) * p.max_r_nnz;
         uint32_t* lend = lend_buf + (b & 1) * p.max_r_nnz;
         uint32_t* ipre = ipre_buf + (b & 1) * (p.max_r_nnz + 1);
@@ -590,11 +591,17 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
             bool ok = false;
             if (p.iiib && lane >= 1 && lane < p.n_levels) ok = theta >= JT<W>::need(st, lane);
             const unsigned m = __ballot_sync(0xffffffffu, ok);
-            const int level = m ? 31 - __clz(m) : 0;
+            const int allowed = m ? 31 - __clz(m) : 0;
+            // theta never falls within a row, so the level warp 0 prepared this block for
+            // (allowed for an earlier theta) is still exact: a block whose allowed level
+            // rose keeps it, and the next block is prepared for the new level, instead of
+            // the whole CTA preparing this block again
+            const int level = (!BF && st.pred_level >= 0 && st.pred_level < allowed) ? st.pred_level : allowed;
             if (lane == 0) {
                 st.floor = fl;
                 JT<W>::theta(st) = theta;
                 st.level = level;
+                st.allowed = allowed;
                 st.need_prepare = !BF && st.pred_level != level;
                 st.pending[b & 1] = 0;
                 st.n_steps++;
@@ -617,20 +624,23 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
             cta_exclusive_scan(ipre, rn, (uint32_t*)red_u);
         }
         // ---- 2. scan: acc[lid] += r[d] * w over the indexed prefixes ----
-        // Each 8-lane sub-warp takes an equal contiguous range of work items, so every
+        // Each 16-lane sub-warp takes an equal contiguous range of work items, so every
         // sub-warp runs the same number of iterations; per item each lane loads U chunks
-        // (one 128-byte line per sub-warp per load) before adding.  Only the last chunk
-        // of a prefix can be partial (lists start on chunk boundaries).
-        // With 4 or more warps, warp 0 instead prepares the next block (for this level)
-        // while the others scan, so that work leaves the critical path.
+        // (two 128-byte lines per sub-warp per load) before adding; one add instruction
+        // covers slot j of 16 consecutive chunks, which the index build placed in distinct
+        // banks where it could.  Only the last chunk of a prefix can be partial (lists
+        // start on chunk boundaries).
+        // With 4 or more warps, warp 0 instead prepares the next block (for the level
+        // the current threshold allows) while the others scan, so that work leaves the
+        // critical path.
         const bool producer = nwarps >= 4;
         if (producer && warp == 0) {
             drain();   // the previous block's deferred candidates
             if (b + 1 < b1 && !BF)
-                prepare_block_warp<V, CH>(p, rf_d, rn, b + 1, level, lbeg_buf + ((b + 1) & 1) * p.max_r_nnz,
+                prepare_block_warp<V, CH>(p, rf_d, rn, b + 1, st.allowed, lbeg_buf + ((b + 1) & 1) * p.max_r_nnz,
                                           lend_buf + ((b + 1) & 1) * p.max_r_nnz,
                                           ipre_buf + ((b + 1) & 1) * (p.max_r_nnz + 1), lane);
-            if (lane == 0) st.pred_level = b + 1 < b1 ? level : -1;
+            if (lane == 0) st.pred_level = b + 1 < b1 ? st.allowed : -1;
         } else if (BF) {
             // Algorithm 2 on the GPU (a baseline): every s of the block is scored in full
             // against r, whose weights are read from the dense copy in shared memory (or by
