@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--learned-full", action="store_true",
                     help="only run the learned-threshold workload at full size (|S| = 5M, 200k training "
                          "and 1M evaluation queries, k = 10) against the plain join, and exit")
+    ap.add_argument("--float-full", action="store_true",
+                    help="only run the float workload at full size (|S| = 10M, |R| = 1M, d = 50,000, "
+                         "k = 20): plain IIIB, learned and batched forms, and exit")
     ap.add_argument("--mlp-gemm", action="store_true",
                     help="only time the learned threshold's tensor-core GEMM (8192 x 256 x 528) and exit")
     ap.add_argument("--float-s", type=int, default=500000, help="|S| of the float scale-up leg")
@@ -387,8 +390,9 @@ def float_leg(args, reps):
     from paper_1011_2807_gb300 import synth
     k = 20
     t0 = time.perf_counter()
-    S = synth.zipf_f32(args.float_s, synth.config_seed(5, "S"))
-    R = synth.zipf_f32(args.float_r, synth.config_seed(5, "R"))
+    procs = max(1, min(16, os.cpu_count() or 1))
+    S = synth.zipf_f32(args.float_s, synth.config_seed(5, "S"), processes=procs)
+    R = synth.zipf_f32(args.float_r, synth.config_seed(5, "R"), processes=procs)
     A = synth.zipf_f32(12000, synth.config_seed(5, "train"))
     gen_s = time.perf_counter() - t0
     idx = knn.knn_join_build_index(S)
@@ -676,6 +680,97 @@ def learned_full(args):
     idx.close()
 
 
+def boundary_ties(pids, psc, oids, osc, rtol=1e-5):
+    """Rows whose ids differ between two float joins of the same rows, and whether every
+    difference is a boundary tie: the ids in one list only, and both lists' k-th scores,
+    lie within rtol (relative) of the row's k-th score, so either list is a correct top-k
+    up to the float tolerance."""
+    import torch
+    rows = torch.nonzero((pids != oids).any(dim=1)).flatten().tolist()
+    ok = True
+    for i in rows:
+        P, X = pids[i].tolist(), oids[i].tolist()
+        sp, sx = psc[i].double().tolist(), osc[i].double().tolist()
+        kth = min(v for v, j in zip(sp, P) if j >= 0)
+        tol = rtol * kth
+        sc = dict(zip(P, sp))
+        sc.update({j: v for j, v in zip(X, sx) if j not in sc})
+        diff = (set(P) ^ set(X)) - {-1}
+        ok &= abs(min(v for v, j in zip(sx, X) if j >= 0) - kth) <= tol
+        ok &= all(abs(sc[j] - kth) <= tol for j in diff)
+    return {"rows": len(rows), "all_boundary_ties": bool(ok)}
+
+
+def float_full(args):
+    """The float workload at its stated size: |S| = 10,000,000 and |R| = 1,000,000 of the
+    Zipf generator (d = 50,000, power-law nnz in [5, 2000], L2-normalised log-normal
+    weights), k = 20.  After a warm-up on the first 65,536 rows, the plain IIIB join, the
+    learned form (trained on 9,000 and calibrated on 3,000 queries of the same generator)
+    and one batched launch of the rows in 8 uneven jobs each join all rows once (CUDA
+    events, nvidia-smi clocks sampled meanwhile); the learned and batched ids are compared
+    with the plain join's (float scores may differ in the last bits with the order of the
+    shared-memory adds)."""
+    import torch
+    import paper_1011_2807_gb300 as knn
+    from paper_1011_2807_gb300 import synth
+    k = 20
+    procs = max(1, min(16, os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    S = synth.zipf_f32(10000000, synth.config_seed(5, "S"), processes=procs)
+    R = synth.zipf_f32(1000000, synth.config_seed(5, "R"), processes=procs)
+    A = synth.zipf_f32(12000, synth.config_seed(5, "train"))
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    idx = knn.knn_join_build_index(S)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Rd = knn.DeviceCSR.from_host(R)
+    Wd = knn.DeviceCSR.from_host(R.slice_rows(0, synth.ZIPF_CHUNK))
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    knn.knn_join(idx, Wd, k, postings_scanned=cnt)
+    torch.cuda.synchronize()
+    post_per_row = int(cnt.item()) / synth.ZIPF_CHUNK
+    Ad = knn.DeviceCSR.from_host(A)
+    _, asc = knn.knn_join(idx, Ad, k)
+    kth = asc[:, k - 1].float()
+    model = knn.ThresholdModel(seed=5)
+    model.train(A.slice_rows(0, 9000), kth[:9000].contiguous(), epochs=15, batch=512, quantile=0.1, seed=5)
+    scale = model.calibrate(A.slice_rows(9000, A.n_rows), kth[9000:].contiguous(), 0.002)
+    knn.knn_join_learned(idx, model, Wd, k)
+    cuts = [0] + sorted(int(R.n_rows * f) for f in (0.02, 0.05, 0.1, 0.2, 0.35, 0.55, 0.75)) + [R.n_rows]
+    parts = [knn.DeviceCSR.from_host(R.slice_rows(a, b)) for a, b in zip(cuts[:-1], cuts[1:])]
+    b = knn.Batch([(idx, P, k) for P in parts], use_graph=True, skip_validation=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    res = {}
+    plain_ms = time_events(lambda: res.update(p=knn.knn_join(idx, Rd, k, skip_validation=True)), 1)
+    learned_ms = time_events(lambda: res.update(l=knn.knn_join_learned(idx, model, Rd, k)), 1)
+    batched_ms = time_events(lambda: b.launch(), 1)
+    clk = clocks.stop()
+    pids, psc = res["p"]
+    lids, lsc, lst = res["l"]
+    bids = torch.cat([o[0] for o in b.outputs])
+    bsc = torch.cat([o[1] for o in b.outputs])
+    n = R.n_rows
+    # 8 B per posting scanned (id, float weight), postings per row from the warm-up rows
+    gbps = post_per_row * 8 * (n / (plain_ms / 1e3)) / 1e9
+    print(json.dumps({
+        "workload": f"float: |S|={S.n_rows:,} (nnz {S.nnz:,}), |R|={n:,} (nnz {R.nnz:,}), d=50,000, "
+                    f"Zipf(1.1) ids, power-law nnz [5, 2000], L2-normalised lognormal float32, k={k}",
+        "plain_iiib_rows_per_s": n / (plain_ms / 1e3), "plain_ms": plain_ms,
+        "postings_per_row_first_65536": post_per_row, "posting_GBps_est": gbps,
+        "learned": {"rows_per_s": n / (learned_ms / 1e3), "speedup": plain_ms / learned_ms,
+                    "fallback_rate": lst["fallback_rows"] / n, "tau_scale": scale,
+                    "other_ids_vs_plain": boundary_ties(pids.cpu(), psc.cpu(), lids.cpu(), lsc.cpu())},
+        "batched": {"jobs": len(parts), "rows_per_s": n / (batched_ms / 1e3), "speedup": plain_ms / batched_ms,
+                    "other_ids_vs_plain": boundary_ties(pids.cpu(), psc.cpu(), bids.cpu(), bsc.cpu())},
+        "index_build_s": build_s, "generate_s": gen_s, "clocks": clk}), flush=True)
+    b.close()
+    model.close()
+    idx.close()
+
+
 def mlp_gemm(args):
     """The learned threshold's first-layer GEMM shape for 8,192 queries, C = A B^T with
     A [8192 x 528], B [256 x 528] in bf16, on the tcgen05 kernel: 3 warm-up calls, then
@@ -711,6 +806,8 @@ def main():
         mlp_gemm(args)
     elif args.learned_full:
         learned_full(args)
+    elif args.float_full:
+        float_full(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -179,7 +179,9 @@ typedef struct {
     int64_t* stats;             /* device int64[KNN_STATS_LEN] or NULL: work counters,
                                    added to (see KNN_STAT_*)                              */
     int32_t blocks_per_launch;  /* with one group per row: S blocks per kernel launch;
-                                   every launch covers all rows (0 = 16)                   */
+                                   every launch covers all rows (0 = as many as keep one
+                                   launch's postings within ~48 MB, so that they stay in
+                                   L2 while every row reads them; at most 16)              */
 } knn_join_opts;
 
 /* Top-k of the union of several S shards (no paper counterpart: the exchange step of
@@ -241,7 +243,8 @@ typedef struct {
     knn_mode mode;
     int32_t threads;            /* threads per CTA for every job, power of two; 0 = 512.
                                    Every job's S block must lie in [4*threads, 64*threads]. */
-    int32_t blocks_per_group;   /* S blocks per work item; 0 = 16                            */
+    int32_t blocks_per_group;   /* S blocks per work item; 0 = as blocks_per_launch's default,
+                                   per job (~48 MB of postings, at most 16)                */
     float level_margin;         /* as in knn_join_opts (0 = 0.3)                             */
     int32_t use_graph;          /* knn_batch_create: capture the launch into a CUDA graph   */
     int32_t skip_validation;    /* 1: trust every R                                          */

@@ -22,7 +22,9 @@ import numpy as np
 
 _lock = threading.Lock()
 
-DEFAULT = {"block_size": 16384, "threads": 512, "blocks_per_launch": 16, "level_margin": 0.3}
+# blocks_per_launch 0: the library's default (as many S blocks as keep a launch's
+# postings within ~48 MB of L2, at most 16)
+DEFAULT = {"block_size": 16384, "threads": 512, "blocks_per_launch": 0, "level_margin": 0.3}
 MARGINS = (0.25, 0.35, 0.45)
 
 

@@ -1154,6 +1154,17 @@ struct SliceRange {
     int64_t b0, b1, g0, g1, p0, p1, f0, f1;   // blocks, S vectors, postings, features
 };
 
+// S blocks per launch (or per batched work item) when the caller gives none: as many as
+// keep one launch's postings within ~48 MB, so that they stay in the 129 MB L2 while
+// every row of the launch reads them; at most 16.  (Spectrum-shaped uint8 S: 2.6 MB of
+// postings per block -> 16; the float workload at |S| = 10M: 7.9 MB per block -> 6.)
+static int default_blocks_per_launch(const knn_index* ix) {
+    const double post_bytes = ix->dtype == KNN_U8 ? 4.0 : 8.0;
+    const double per_block = (double)ix->n_postings * post_bytes / (double)std::max(1, ix->n_blocks);
+    const int b = per_block > 0.0 ? (int)std::min(16.0, 48.0e6 / per_block) : 16;
+    return std::max(1, b);
+}
+
 static SliceRange slice_of(const knn_index* ix, int li, int per_launch) {
     SliceRange r;
     r.b0 = (int64_t)li * per_launch;
@@ -1358,7 +1369,8 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     KNN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     // One group per row: S-block-synchronous launches.  Every launch walks all rows over
     // the same few S blocks, so their postings stay in L2 while all rows read them.
-    int per_launch = groups == 1 ? (o.blocks_per_launch > 0 ? o.blocks_per_launch : 16) : ix->n_blocks;
+    int per_launch = groups == 1 ? (o.blocks_per_launch > 0 ? o.blocks_per_launch : default_blocks_per_launch(ix))
+                                 : ix->n_blocks;
     per_launch = std::min(per_launch, ix->n_blocks);
     const int n_launch = groups == 1 ? (int)ceil_div(ix->n_blocks, per_launch) : 1;
     if (n_launch > 1) KNN_TRY(tmp.get(&p.carry, (size_t)r.n_rows * k));
@@ -1572,7 +1584,8 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
 
     const JoinKernel kern = join_kernel(ix->dtype, p.touched || p.stats, p.bf != 0);
     KNN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-    const int per_launch = std::min(ix->n_blocks, o.blocks_per_launch > 0 ? o.blocks_per_launch : 16);
+    const int per_launch =
+        std::min(ix->n_blocks, o.blocks_per_launch > 0 ? o.blocks_per_launch : default_blocks_per_launch(ix));
     const int n_launch = (int)ceil_div(ix->n_blocks, per_launch);
     for (int li = 0; li < n_launch; li++) {
         p.block_begin = li * per_launch;
@@ -1672,7 +1685,6 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
     if (T < 64 || T > 1024 || (T & 31) || (T & (T - 1)))
         return bail(fail(KNN_EINVAL, "threads must be a power of two in [64, 1024]"));
     b->T = T;
-    const int bpg_opt = o.blocks_per_group > 0 ? o.blocks_per_group : 16;
 
     Buffers tmp(stream);
     struct JobPlan {
@@ -1712,7 +1724,7 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
         if (sm + sizeof(CtaState) + 32 * 8 * 2 + 128 > (size_t)smem_optin)
             return bail(fail(KNN_EUNSUPPORTED, "job %d: needs %zu bytes of shared memory", j, sm));
         smem_max = std::max(smem_max, sm);
-        int bpg = std::min(bpg_opt, ix->n_blocks);
+        int bpg = std::min(o.blocks_per_group > 0 ? o.blocks_per_group : default_blocks_per_launch(ix), ix->n_blocks);
         int groups = (int)ceil_div(ix->n_blocks, bpg);
 
         JoinParams& p = hj[j].p;
