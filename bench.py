@@ -421,7 +421,8 @@ def float_leg(args, reps):
     # up to summation order; count rows whose ids differ
     out["learned"] = {"speedup": plain_ms / l_ms, "fallback_rate": lst["fallback_rows"] / R.n_rows,
                       "tau_scale": scale,
-                      "rows_with_other_ids": int((lids != ref_ids).any(dim=1).sum().item())}
+                      "rows_with_other_ids": int((lids != ref_ids).any(dim=1).sum().item()),
+                      "other_ids_vs_plain": boundary_ties(ref_ids.cpu(), ref_sc.cpu(), lids.cpu(), lsc.cpu())}
     model.close()
     # batched: the rows in 8 uneven jobs against the same index, one persistent launch
     cuts = [0] + sorted(int(R.n_rows * f) for f in (0.02, 0.05, 0.1, 0.2, 0.35, 0.55, 0.75)) + [R.n_rows]
@@ -432,8 +433,10 @@ def float_leg(args, reps):
     b_ms = time_events(lambda: b.launch(), reps)
     sep_ms = time_events(lambda: [knn.knn_join(idx, P, k, skip_validation=True) for P in parts], reps)
     bids = torch.cat([o[0] for o in b.outputs])
+    bsc = torch.cat([o[1] for o in b.outputs])
     out["batched"] = {"jobs": len(parts), "speedup_vs_separate_calls": sep_ms / b_ms,
-                      "rows_with_other_ids": int((bids != ref_ids).any(dim=1).sum().item())}
+                      "rows_with_other_ids": int((bids != ref_ids).any(dim=1).sum().item()),
+                      "other_ids_vs_plain": boundary_ties(ref_ids.cpu(), ref_sc.cpu(), bids.cpu(), bsc.cpu())}
     b.close()
     out["plain_iiib_ms"] = plain_ms
     idx.close()
