@@ -572,8 +572,8 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     for (int b = (rn > 0 ? b0 : b1); b < b1; b++) {
         // ---- 1. level (warp 0: lane l tests level l) ----
         // The list ranges and work items of this block were prepared by warp 0 during the
-        // previous block's scan, for the level that block used; they are prepared here,
-        // by the whole CTA, only for a launch's first block or when the level changed.
+        // previous block's scan, for the level the threshold then allowed; they are
+        // prepared here, by the whole CTA, only for a launch's first block.
         constexpr int V = JT<W>::PER_VEC;   // postings per 16-byte chunk
         constexpr int G = 16, U = 4, CH = G * U;
         uint32_t* lbeg = lbeg_buf + (b & 1) * p.max_r_nnz;
