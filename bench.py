@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--no-bf", action="store_true", help="skip the brute-force comparison")
     ap.add_argument("--no-float", action="store_true", help="skip the float scale-up leg")
     ap.add_argument("--no-host-index", action="store_true", help="skip the host-resident index leg")
+    ap.add_argument("--no-iib", action="store_true", help="skip the unrefined (IIB) comparison on the main workload")
+    ap.add_argument("--no-learned-full-leg", action="store_true",
+                    help="skip the learned-threshold workload at full size inside the main line")
+    ap.add_argument("--no-float-full-leg", action="store_true",
+                    help="skip the float workload at full size inside the main line")
     ap.add_argument("--learned-full", action="store_true",
                     help="only run the learned-threshold workload at full size (|S| = 5M, 200k training "
                          "and 1M evaluation queries, k = 10) against the plain join, and exit")
@@ -131,6 +136,14 @@ def measured_peak():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def measured_sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
 
 
 def profiled_traffic(kernel_src):
@@ -276,30 +289,30 @@ def time_events(fn, reps):
     return statistics.median(ms)
 
 
-def batched_leg(args, R, S, reps):
-    """64 uneven joins (config-3 sizes; S = leading rows of the benchmark's S, R = windows
-    of its R) as one persistent launch replayed from a CUDA graph, against the same
-    joins as 64 separate knn_join calls.  Block sizes are autotuned per |S| class."""
+def batched_leg(args, reps):
+    """The 64 uneven joins of the batched workload (|R| log-U[100, 50k], |S| log-U[1e4,
+    1e6], k in {1,5,10,20,50}, each job's R and S from its own seeded generator) as one
+    persistent launch replayed from a CUDA graph, against the same joins as 64 separate
+    knn_join calls.  S-block sizes and blocks per launch are autotuned per |S| class."""
     import torch
     import paper_1011_2807_gb300 as knn
     from paper_1011_2807_gb300 import autotune, synth
     spec = synth.config3_jobs(args.batch_jobs)
     t0 = time.perf_counter()
+    procs = max(1, min(16, os.cpu_count() or 1))
+    data = synth.generate([("config3_job_data", (js,)) for js in spec], processes=procs)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
     tuned = {}
     jobs = []
-    for j, js in enumerate(spec):
-        n_s = min(js["n_s"], S.n_rows)
-        n_r = min(js["n_r"], R.n_rows)
-        o = (j * 7919) % max(1, R.n_rows - n_r + 1)
-        Sj = S.slice_rows(0, n_s)
-        Rj = R.slice_rows(o, o + n_r)
-        key = round(math.log2(max(2, n_s)))
+    for (Rj, Sj, k) in data:
+        key = round(math.log2(max(2, Sj.n_rows)))
         if key not in tuned:
-            tuned[key] = autotune.tune(Sj, Rj.slice_rows(0, min(256, n_r)), js["k"], threads=512, reps=1,
+            tuned[key] = autotune.tune(Sj, Rj.slice_rows(0, min(256, Rj.n_rows)), k, threads=512, reps=1,
                                        max_trials=12)
         cfg = tuned[key]
         idx = knn.knn_join_build_index(Sj, block_size=cfg["block_size"])
-        jobs.append(dict(idx=idx, Rd=knn.DeviceCSR.from_host(Rj), k=js["k"], n_r=n_r, n_s=n_s,
+        jobs.append(dict(idx=idx, Rd=knn.DeviceCSR.from_host(Rj), k=k, n_r=Rj.n_rows, n_s=Sj.n_rows,
                          bpl=cfg["blocks_per_launch"]))
     setup_s = time.perf_counter() - t0
     for jb in jobs:   # validate every R once
@@ -329,13 +342,15 @@ def batched_leg(args, R, S, reps):
     b.close()
     for jb in jobs:
         jb["idx"].close()
-    return {"jobs": len(jobs), "rows": rows, "plain_ms": plain_ms, "batched_ms": batched_ms,
+    return {"jobs": len(jobs), "rows": rows, "s_vectors": sum(jb["n_s"] for jb in jobs),
+            "plain_ms": plain_ms, "batched_ms": batched_ms,
             "plain_rows_per_s": rows / (plain_ms / 1e3), "batched_rows_per_s": rows / (batched_ms / 1e3),
             "speedup": plain_ms / batched_ms, "identical": identical, "graph": bool(info["graph"]),
             "work_items": info["work_items"], "kernels_per_launch": launches, "setup_s": setup_s,
-            "autotuned_block_sizes": sorted({v["block_size"] for v in tuned.values()}),
-            "workload": "config-3 sizes: |R| log-U[100, 50k], |S| log-U[1e4, 1e6], k in {1,5,10,20,50}; "
-                        "S = leading rows of the benchmark S, R = windows of the benchmark R"}
+            "generate_s": gen_s,
+            "autotuned": {str(k): v for k, v in sorted(tuned.items())},
+            "workload": "64 joins: |R| log-U[100, 50k], |S| log-U[1e4, 1e6] (spectrum-shaped uint8, "
+                        "each job from its own seeded generator), k in {1,5,10,20,50}"}
 
 
 def host_index_leg(args, S, Rd, ids, sc, plain_ms, reps):
@@ -425,8 +440,7 @@ def float_leg(args, reps):
                       "other_ids_vs_plain": boundary_ties(ref_ids.cpu(), ref_sc.cpu(), lids.cpu(), lsc.cpu())}
     model.close()
     # batched: the rows in 8 uneven jobs against the same index, one persistent launch
-    cuts = [0] + sorted(int(R.n_rows * f) for f in (0.02, 0.05, 0.1, 0.2, 0.35, 0.55, 0.75)) + [R.n_rows]
-    parts = [knn.DeviceCSR.from_host(R.slice_rows(a, b)) for a, b in zip(cuts[:-1], cuts[1:])]
+    parts = [knn.DeviceCSR.from_host(R.slice_rows(a, b)) for a, b in uneven_parts(R.n_rows)]
     b = knn.Batch([(idx, P, k) for P in parts], use_graph=True, skip_validation=True)
     b.launch()
     torch.cuda.synchronize()
@@ -443,7 +457,7 @@ def float_leg(args, reps):
     return out
 
 
-def learned_leg(args, R, S, idx, Rd, ids, sc, plain_ms, reps):
+def learned_leg(args, R, S, idx, Rd, ids, sc, plain_ms, plain_scanned, reps):
     """Learned start threshold: train on exact k-th scores of fresh queries from the same
     generator, then join the benchmark R from the predictions (verify-and-fallback)."""
     import torch
@@ -484,7 +498,9 @@ def learned_leg(args, R, S, idx, Rd, ids, sc, plain_ms, reps):
     return {"rows_per_s": R.n_rows / (learned_ms / 1e3), "plain_rows_per_s": R.n_rows / (plain_ms / 1e3),
             "speedup": plain_ms / learned_ms, "identical": identical,
             "fallback_rate": st.get("fallback_rows", 0) / max(1, R.n_rows),
-            "postings_scanned": int(c_l.item()), "train_queries": T.n_rows, "calibration_queries": V.n_rows,
+            "postings_scanned": int(c_l.item()), "plain_postings_scanned": plain_scanned,
+            "postings_ratio_vs_plain": int(c_l.item()) / max(1, plain_scanned),
+            "train_queries": T.n_rows, "calibration_queries": V.n_rows,
             "tau_scale": scale, "train_s": train_s, "label_join_s": label_s, "final_loss": loss, "quantile": 0.1}
 
 
@@ -519,9 +535,11 @@ def run_ours(args):
               out_scores=sc)
     # validate R once, and count the postings one step scans
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-    knn.knn_join(idx, Rd, k, postings_scanned=cnt, **kw)
+    stats = torch.zeros(len(knn.binding.KNN_STATS), dtype=torch.int64, device="cuda")
+    knn.knn_join(idx, Rd, k, postings_scanned=cnt, stats=stats, **kw)
     torch.cuda.synchronize()
     scanned = int(cnt.item())
+    work = dict(zip(knn.binding.KNN_STATS, stats.cpu().tolist()))
     p_iib = iib_postings(R, S)
 
     for _ in range(args.warmup):
@@ -576,29 +594,64 @@ def run_ours(args):
         # results of the two paths agree
         assert torch.equal(hid, ids.cpu()) and torch.equal(hsc, sc.cpu())
 
-    # roofline of the dominant kernel (the join; index build excluded)
-    peak, peak_src = measured_peak()
+    # roofline of the dominant kernel (the join; index build excluded).  The scan adds
+    # every posting into a shared-memory accumulator with red.shared.add, and ncu shows
+    # the shared-memory pipe, not DRAM, as the busiest unit (L2 serves the postings), so
+    # the bound is the shared-memory atomic pipe: at most one wavefront per SM per cycle,
+    # i.e. 32 adds per SM per cycle when the 32 lanes of an add hit 32 distinct banks.
+    hbm_peak, peak_src = measured_peak()
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    sm_mhz = (clk or {}).get("sm_mhz") or measured_sm_max_mhz()
+    kern_ms = statistics.mean(step_ms)
+    kern_s = kern_ms / 1000.0
+    adds = work["shared_adds"]
+    peak_gadds = n_sm * sm_mhz * 1e6 * 32 / 1e9
+    achieved_gadds = adds / kern_s / 1e9
     bytes_post = 4 * scanned
     bytes_r = R.indices.nbytes + R.values.nbytes + R.indptr.nbytes
     bytes_out = R.n_rows * k * 8
     alg_bytes = bytes_post + bytes_r + bytes_out
-    kern_ms = statistics.mean(step_ms)
-    achieved = alg_bytes / (kern_ms / 1000.0) / 1e9   # = bytes per launch / mean launch time
     launches_per_step = max(1, launches // max(1, args.steps))   # k_join launches + R's row statistics
     join_launches = -(-info["n_blocks"] // max(1, args.blocks_per_launch))
     traffic, traffic_note = profiled_traffic(os.path.join(ROOT, "paper_1011_2807_gb300", "csrc", "join.cu"))
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
+    launch_s = kern_s / join_launches
+    roofline = {"bound": "smem_atomic", "achieved": achieved_gadds, "peak": peak_gadds, "unit": "Gadd/s",
+                "frac": achieved_gadds / peak_gadds, "traffic": traffic,
                 "kernel": "k_join (posting scan + accumulate + select + top-k, fused)",
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_step": alg_bytes, "kernel_launches_per_step": launches_per_step,
-                "k_join_launches_per_step": join_launches,
+                "peak_source": f"derived: {n_sm} SMs x {sm_mhz:.0f} MHz (median SM clock in the timed region) x 32 "
+                               "adds per conflict-free red.shared wavefront, one wavefront per SM per cycle",
+                "achieved_from": "shared-memory adds issued per step (KNN_STAT_SHARED_ADDS: every posting slot "
+                                 "of the 16-byte chunks read, padding included) / mean step time",
+                "shared_adds_per_step": adds, "postings_scanned_per_step": scanned,
+                "kernel_launches_per_step": launches_per_step, "k_join_launches_per_step": join_launches,
+                "posting_bytes_GBps": alg_bytes / kern_s / 1e9,
+                "posting_bytes_per_unit": "4 B per posting scanned + 5 B per R feature + 8 B per R row index "
+                                          "+ 8k B output (algorithmic; L2 serves the postings to every row)",
                 "algorithmic_bytes_per_launch": alg_bytes / join_launches,
+                "hbm_peak_GBps": hbm_peak,
+                "hbm_peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                                   else "fallback 6.8 TB/s",
                 "traffic_unit": "DRAM bytes read + written per k_join launch (ncu, full-size launch)",
-                "bytes_per_unit": "4 B per posting scanned + 5 B per R feature + 8 B per R row index + 8k B output",
-                "iib_equivalent_GBps": (4 * p_iib + bytes_r + bytes_out) / (kern_ms / 1000.0) / 1e9}
+                "iib_equivalent_GBps": (4 * p_iib + bytes_r + bytes_out) / kern_s / 1e9}
+    if traffic is not None:
+        roofline["dram_GBps"] = traffic / launch_s / 1e9
+        roofline["dram_frac"] = roofline["dram_GBps"] / hbm_peak
     if traffic_note:
         roofline["traffic_note"] = traffic_note
+
+    iib = None
+    if rank == 0 and world == 1 and not args.no_iib:
+        c_iib = torch.zeros(1, dtype=torch.int64, device="cuda")
+        iids, isc = knn.knn_join(idx, Rd, k, mode="iib", threads=args.threads,
+                                 blocks_per_launch=args.blocks_per_launch, postings_scanned=c_iib)
+        torch.cuda.synchronize()
+        iib_ms = time_events(lambda: knn.knn_join(idx, Rd, k, mode="iib", threads=args.threads,
+                                                  blocks_per_launch=args.blocks_per_launch, skip_validation=True), 3)
+        iib = {"iib_rows_per_s": R.n_rows / (iib_ms / 1e3), "iiib_rows_per_s": R.n_rows / kern_s,
+               "iiib_speedup": iib_ms / kern_ms, "iib_postings_scanned": int(c_iib.item()),
+               "iiib_postings_scanned": scanned, "iiib_postings_ratio": scanned / max(1, int(c_iib.item())),
+               "identical": bool(torch.equal(iids, ids) and torch.equal(isc, sc))}
 
     batched = learned = bf = flt = host = None
     if rank == 0 and world == 1 and not args.no_host_index:
@@ -606,12 +659,17 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_bf:
         bf = bf_leg(args, R, idx, reps=2)
     if rank == 0 and world == 1 and not args.no_learned:
-        learned = learned_leg(args, R, S, idx, Rd, ids, sc, kern_ms, reps=3)
+        learned = learned_leg(args, R, S, idx, Rd, ids, sc, kern_ms, scanned, reps=3)
     if rank == 0 and world == 1 and not args.no_batched:
-        batched = batched_leg(args, R, S, reps=3)
+        batched = batched_leg(args, reps=3)
 
     if rank == 0 and world == 1 and not args.no_float:
         flt = float_leg(args, reps=3)
+    lfull = ffull = None
+    if rank == 0 and world == 1 and not args.no_learned_full_leg:
+        lfull = learned_full(args)
+    if rank == 0 and world == 1 and not args.no_float_full_leg:
+        ffull = float_full(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -637,6 +695,8 @@ def run_ours(args):
                 "gpu_launches": launches, "roofline": roofline, "clocks": clk,
                 "e2e": e2e, "cpu_baseline": cpu, "learned_vs_plain": learned, "batched_vs_plain": batched,
                 "bf_vs_plain": bf, "float_scaleup": flt, "host_resident_index": host,
+                "iib_vs_iiib": iib, "learned_workload_full": lfull, "float_workload_full": ffull,
+                "work_counters_per_step": work,
                 "kernel_ms_per_step": kern_ms}
         print(json.dumps(line), flush=True)
     idx.close()
@@ -644,17 +704,30 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def uneven_parts(n):
+    """Row ranges of 8 uneven jobs covering n rows (2 %, 3 %, 5 %, 10 %, 15 %, 20 %, 20 %,
+    25 %)."""
+    cuts = [0] + sorted(int(n * f) for f in (0.02, 0.05, 0.1, 0.2, 0.35, 0.55, 0.75)) + [n]
+    return list(zip(cuts[:-1], cuts[1:]))
+
+
 def learned_full(args):
     """The learned-threshold workload at its stated size: |S| = 5,000,000 and 1,000,000
     evaluation queries of the spectrum-shaped generator, k = 10; the model trains on
     190,000 exact (query, k-th score) pairs and calibrates on 10,000 more (0.2 %
-    fallback target); plain and learned joins of the evaluation queries are timed with
-    CUDA events (1 warm-up, 2 timed) and their results compared."""
+    fallback target); the plain join, the learned join and one batched launch of the
+    evaluation rows in 8 uneven jobs are timed with CUDA events (1 warm-up, 2 timed)
+    and their results compared (uint8: bit-exact)."""
     import torch
     import paper_1011_2807_gb300 as knn
     from paper_1011_2807_gb300 import synth
     t0 = time.perf_counter()
-    T, E, S, k = synth.config4()
+    T, E, S = synth.generate([
+        ("spectrum_u8", (200000, synth.config_seed(4, "train")), {"role": "R"}),
+        ("spectrum_u8", (1000000, synth.config_seed(4, "eval")), {"role": "R"}),
+        ("spectrum_u8", (5000000, synth.config_seed(4, "S")), {"role": "S"}),
+    ], processes=3)
+    k = 10
     gen_s = time.perf_counter() - t0
     idx = knn.knn_join_build_index(S)
     Td, Ed = knn.DeviceCSR.from_host(T), knn.DeviceCSR.from_host(E)
@@ -662,25 +735,43 @@ def learned_full(args):
     lab = tsc[:, k - 1].float()
     n_fit = T.n_rows - 10000
     model = knn.ThresholdModel(seed=1)
+    t1 = time.perf_counter()
     loss = model.train(T.slice_rows(0, n_fit), lab[:n_fit].contiguous(), epochs=15, batch=512, quantile=0.1, seed=1)
     scale = model.calibrate(T.slice_rows(n_fit, T.n_rows), lab[n_fit:].contiguous(), 0.002)
-    pids, psc = knn.knn_join(idx, Ed, k)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    c_p = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pids, psc = knn.knn_join(idx, Ed, k, postings_scanned=c_p)
     torch.cuda.synchronize()
     plain_ms = time_events(lambda: knn.knn_join(idx, Ed, k, skip_validation=True), 2)
-    res = {}
-    res["o"] = knn.knn_join_learned(idx, model, Ed, k)
+    c_l = torch.zeros(1, dtype=torch.int64, device="cuda")
+    res = {"o": knn.knn_join_learned(idx, model, Ed, k, postings_scanned=c_l)}
     torch.cuda.synchronize()
     learned_ms = time_events(lambda: res.update(o=knn.knn_join_learned(idx, model, Ed, k)), 2)
     lids, lsc, st = res["o"]
-    print(json.dumps({
+    parts = [knn.DeviceCSR.from_host(E.slice_rows(a, b)) for a, b in uneven_parts(E.n_rows)]
+    bt = knn.Batch([(idx, P, k) for P in parts], use_graph=True, skip_validation=True)
+    bt.launch()
+    torch.cuda.synchronize()
+    batched_ms = time_events(lambda: bt.launch(), 2)
+    bids = torch.cat([o[0] for o in bt.outputs])
+    bsc = torch.cat([o[1] for o in bt.outputs])
+    n = E.n_rows
+    out = {
         "workload": f"learned threshold: |S|={S.n_rows:,}, {n_fit:,} training + 10,000 calibration queries, "
-                    f"{E.n_rows:,} evaluation queries, k={k}, spectrum-shaped uint8",
-        "plain_rows_per_s": E.n_rows / (plain_ms / 1e3), "learned_rows_per_s": E.n_rows / (learned_ms / 1e3),
-        "speedup": plain_ms / learned_ms, "identical": bool(torch.equal(pids, lids) and torch.equal(psc, lsc)),
-        "fallback_rate": st["fallback_rows"] / E.n_rows, "tau_scale": scale, "final_loss": loss,
-        "generate_s": gen_s}), flush=True)
+                    f"{n:,} evaluation queries, k={k}, spectrum-shaped uint8",
+        "plain_rows_per_s": n / (plain_ms / 1e3),
+        "learned": {"rows_per_s": n / (learned_ms / 1e3), "speedup": plain_ms / learned_ms,
+                    "identical": bool(torch.equal(pids, lids) and torch.equal(psc, lsc)),
+                    "fallback_rate": st["fallback_rows"] / n, "tau_scale": scale, "final_loss": loss,
+                    "postings_ratio_vs_plain": int(c_l.item()) / max(1, int(c_p.item())), "train_s": train_s},
+        "batched": {"jobs": len(parts), "rows_per_s": n / (batched_ms / 1e3), "speedup": plain_ms / batched_ms,
+                    "identical": bool(torch.equal(pids, bids) and torch.equal(psc, bsc))},
+        "generate_s": gen_s}
+    bt.close()
     model.close()
     idx.close()
+    return out
 
 
 def boundary_ties(pids, psc, oids, osc, rtol=1e-5):
@@ -712,7 +803,7 @@ def float_full(args):
     and one batched launch of the rows in 8 uneven jobs each join all rows once (CUDA
     events, nvidia-smi clocks sampled meanwhile); the learned and batched ids are compared
     with the plain join's (float scores may differ in the last bits with the order of the
-    shared-memory adds)."""
+    shared-memory adds: every differing row must be a boundary tie)."""
     import torch
     import paper_1011_2807_gb300 as knn
     from paper_1011_2807_gb300 import synth
@@ -739,9 +830,9 @@ def float_full(args):
     model = knn.ThresholdModel(seed=5)
     model.train(A.slice_rows(0, 9000), kth[:9000].contiguous(), epochs=15, batch=512, quantile=0.1, seed=5)
     scale = model.calibrate(A.slice_rows(9000, A.n_rows), kth[9000:].contiguous(), 0.002)
-    knn.knn_join_learned(idx, model, Wd, k)
-    cuts = [0] + sorted(int(R.n_rows * f) for f in (0.02, 0.05, 0.1, 0.2, 0.35, 0.55, 0.75)) + [R.n_rows]
-    parts = [knn.DeviceCSR.from_host(R.slice_rows(a, b)) for a, b in zip(cuts[:-1], cuts[1:])]
+    c_l = torch.zeros(1, dtype=torch.int64, device="cuda")
+    knn.knn_join_learned(idx, model, Wd, k, postings_scanned=c_l)
+    parts = [knn.DeviceCSR.from_host(R.slice_rows(a, b)) for a, b in uneven_parts(R.n_rows)]
     b = knn.Batch([(idx, P, k) for P in parts], use_graph=True, skip_validation=True)
     torch.cuda.synchronize()
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
@@ -758,20 +849,22 @@ def float_full(args):
     n = R.n_rows
     # 8 B per posting scanned (id, float weight), postings per row from the warm-up rows
     gbps = post_per_row * 8 * (n / (plain_ms / 1e3)) / 1e9
-    print(json.dumps({
+    out = {
         "workload": f"float: |S|={S.n_rows:,} (nnz {S.nnz:,}), |R|={n:,} (nnz {R.nnz:,}), d=50,000, "
                     f"Zipf(1.1) ids, power-law nnz [5, 2000], L2-normalised lognormal float32, k={k}",
         "plain_iiib_rows_per_s": n / (plain_ms / 1e3), "plain_ms": plain_ms,
         "postings_per_row_first_65536": post_per_row, "posting_GBps_est": gbps,
         "learned": {"rows_per_s": n / (learned_ms / 1e3), "speedup": plain_ms / learned_ms,
                     "fallback_rate": lst["fallback_rows"] / n, "tau_scale": scale,
+                    "postings_ratio_vs_plain_first_65536": int(c_l.item()) / max(1, int(cnt.item())),
                     "other_ids_vs_plain": boundary_ties(pids.cpu(), psc.cpu(), lids.cpu(), lsc.cpu())},
         "batched": {"jobs": len(parts), "rows_per_s": n / (batched_ms / 1e3), "speedup": plain_ms / batched_ms,
                     "other_ids_vs_plain": boundary_ties(pids.cpu(), psc.cpu(), bids.cpu(), bsc.cpu())},
-        "index_build_s": build_s, "generate_s": gen_s, "clocks": clk}), flush=True)
+        "index_build_s": build_s, "generate_s": gen_s, "clocks": clk}
     b.close()
     model.close()
     idx.close()
+    return out
 
 
 def mlp_gemm(args):
@@ -808,9 +901,9 @@ def main():
     if args.mlp_gemm:
         mlp_gemm(args)
     elif args.learned_full:
-        learned_full(args)
+        print(json.dumps(learned_full(args)), flush=True)
     elif args.float_full:
-        float_full(args)
+        print(json.dumps(float_full(args)), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

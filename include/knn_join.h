@@ -208,7 +208,10 @@ knn_status knn_merge_topk(int32_t n_parts, const int32_t* const* part_ids, const
 #define KNN_STAT_ROUNDS 5           /* extra candidate rounds (push buffer full)            */
 #define KNN_STAT_RESIDUAL_FEATURES 6 /* unindexed features merged in completions            */
 #define KNN_STAT_POSTINGS 7         /* postings scanned                                     */
-#define KNN_STATS_LEN 8
+#define KNN_STAT_SHARED_ADDS 8      /* shared-memory adds issued by the scan: every posting
+                                       slot of the 16-byte chunks read, the zero-weight
+                                       padding and the slots past a level's prefix included */
+#define KNN_STATS_LEN 9
 
 /* Exact top-k of every row of R against the indexed S.
  *   index       built by knn_join_build_index (same dim and dtype as R).
@@ -405,11 +408,13 @@ knn_status knn_threshold_model_params(const knn_model* model, const float** para
  *   - rows are always scanned with one S-block group per row (s_groups is ignored);
  *   - n_rows * k must not exceed (KNN_NOALLOC_SCRATCH_BYTES - 256) / 8 = 2,097,120,
  *     else KNN_EUNSUPPORTED with a message naming the limit.
- * The first call on a device (with that device current) looks up the array's device
- * address with cudaGetSymbolAddress; make that first call before any stream capture.
+ * Set-up: the first call on a device (with that device current) looks up the array's
+ * device address with cudaGetSymbolAddress and keeps it; make that first call before
+ * any stream capture begins.  Every call, the first and the later ones, synchronises
+ * `stream`: it reads R's size and longest row back to the host.
  * All calls share the array and it keeps the last call's contents: calls that overlap
  * on the GPU (other streams or host threads) race on it and must be serialised by the
- * caller.  Synchronises `stream` (it reads R's size and longest row back).          */
+ * caller.                                                                           */
 knn_status knn_join_noalloc(const knn_index* index, const knn_csr* R, int32_t k,
                             const knn_join_opts* opts, int32_t* out_ids, void* out_scores,
                             void* stream);

@@ -66,7 +66,7 @@ class _JoinOpts(ctypes.Structure):
                 ("stats", ctypes.c_void_p), ("blocks_per_launch", ctypes.c_int32)]
 
 KNN_STATS = ("block_steps", "candidates", "completed", "pushed", "merges", "rounds",
-             "residual_features", "postings")
+             "residual_features", "postings", "shared_adds")
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

@@ -69,9 +69,10 @@ struct JT<uint8_t> {
         if (c >= 4294967295.0) return (u64)0xFFFFFFFFull << 32;
         return (u64)(uint32_t)c << 32;
     }
-    static constexpr double SLACK = 0.0;
+    // integer sums are exact: no rounding error to allow for
+    __device__ static double gamma(int n) { return 0.0; }
     // bound on the unindexed residual at a level: M * (largest integer weight sum <= L)
-    __device__ static double level_bound(double M, float L) { return M * floor((double)L); }
+    __device__ static double level_bound(double M, float L, double g) { return M * floor((double)L); }
     // smallest partial score whose upper bound (partial + lb) reaches theta
     __device__ static int32_t cheap_min(double theta, double lb) {
         double c = ceil(theta - lb);
@@ -79,7 +80,7 @@ struct JT<uint8_t> {
         if (c > 2147483647.0) c = 2147483647.0;
         return (int32_t)c;
     }
-    __device__ static bool exact_ok(int32_t v, double M, uint32_t ub_bits, double theta) {
+    __device__ static bool exact_ok(int32_t v, double M, uint32_t ub_bits, double theta, double g) {
         return (double)v + M * (double)ub_bits >= theta;
     }
     template <class S>
@@ -136,16 +137,31 @@ struct JT<float> {
         if (!(tau > 0.0f)) return (u64)1 << 32;
         return (u64)__float_as_uint(tau) << 32;
     }
-    // fp32 sums may differ from the real sum by a few ulps; widen bounds a little
-    static constexpr double SLACK = 1.0 / (1 << 20);
-    __device__ static double level_bound(double M, float L) { return M * (double)L * (1.0 + SLACK); }
+    // Rounding.  A candidate's score is F = fl(v + res): v its fp32 partial (compared as
+    // computed, so its own rounding needs no allowance), res the fp32 dot over its
+    // unindexed features.  res has at most n = nnz(r) nonzero terms (a feature missing
+    // from r adds an exact 0), so for any summation order res <= Q (1 + gamma_n), Q the
+    // real residual, with gamma_n = n u / (1 - n u), u = 2^-24 (the standard bound for n
+    // roundings of nonnegative terms); a further 2^-40 covers the double arithmetic of
+    // the bounds themselves.  The final add gives F <= (v + res)(1 + u).
+    static constexpr double SLACK = 1.0 / (1 << 20);   // >= 2u: room for the final add
+    __device__ static double gamma(int n) {
+        const double nu = (double)(n + 1) * (1.0 / 16777216.0);
+        return nu / (1.0 - nu) + 1.0 / 1099511627776.0;
+    }
+    // bound on the computed residual at a level: M * L * (1 + gamma)
+    __device__ static double level_bound(double M, float L, double g) { return M * (double)L * (1.0 + g); }
+    // a partial v below this cannot give F >= theta: v < theta (1 - SLACK) - lb implies
+    // (v + lb)(1 + u) < theta
     __device__ static float cheap_min(double theta, double lb) {
-        double c = (theta - lb) * (1.0 - SLACK);
+        double c = theta * (1.0 - SLACK) - lb;
         float f = c > 0.0 ? __double2float_rd(c) : 0.0f;
         return fmaxf(f, 1.40129846e-45f);   // candidates are always > 0
     }
-    __device__ static bool exact_ok(float v, double M, uint32_t ub_bits, double theta) {
-        return ((double)v + M * (double)__uint_as_float(ub_bits)) * (1.0 + SLACK) >= theta;
+    // F can reach theta: (v + M ub)(1 + gamma) >= theta, with gamma >= u also covering the
+    // final add
+    __device__ static bool exact_ok(float v, double M, uint32_t ub_bits, double theta, double g) {
+        return ((double)v + M * (double)__uint_as_float(ub_bits)) * (1.0 + g) >= theta;
     }
     template <class S>
     __device__ static void set_cmin(S& st, float c) { st.cmin_f = c; }
@@ -169,7 +185,7 @@ struct JT<float> {
     __device__ static Th bound_up(double lb) { return __double2float_ru(lb); }
     // cheap_min from the bound rounded up, rounding down: at most its double value
     __device__ static float cheap_min_th(Th theta, Th lbu) {
-        const float c = __fmul_rd(__fsub_rd(theta, lbu), 1.0f - 1.0f / 1048576.0f);   // 1 - SLACK
+        const float c = __fsub_rd(__fmul_rd(theta, 1.0f - 1.0f / 1048576.0f), lbu);   // theta (1 - SLACK) - lb
         return fmaxf(c, 1.40129846e-45f);
     }
     template <class S>
@@ -268,6 +284,7 @@ struct CtaState {
     u64 floor;      // keys below this never qualify
     u64 kth;        // current k-th key (0 while fewer than k)
     double M;       // largest weight of r
+    double g;       // relative rounding allowance of a completed score (0 for integers)
     double lb;      // residual bound of the current level (0 at level 0)
     float cmin_f;   // smallest partial score worth a look in this block (as float/int)
     int32_t cmin_i;
@@ -464,14 +481,16 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     if (warp == 0) {
         const double m = (double)JT<W>::value_of_bits(
             __reduce_max_sync(0xffffffffu, lane < nwarps ? red_m[lane] : 0u));
+        const double g = JT<W>::gamma(rn);
         if (lane < p.n_levels) {   // lane l: level l's bound and the thresholds derived from it
-            const double lb = lane ? JT<W>::level_bound(m, p.levels[lane]) : 0.0;
+            const double lb = lane ? JT<W>::level_bound(m, p.levels[lane], g) : 0.0;
             st.lbnd[lane] = lb;
             JT<W>::need(st, lane) = JT<W>::level_need(lb, p.level_margin);
             JT<W>::lbu(st, lane) = JT<W>::bound_up(lb);
         }
         if (lane == 0) {
             st.M = m;
+            st.g = g;
             st.size = 0;
             st.cnt = 0;
             st.kth = 0ull;
@@ -495,7 +514,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     __syncthreads();
 
     uint32_t n_cand = 0, n_comp = 0, n_push = 0, n_resf = 0;   // this thread's counters
-    unsigned long long n_post = 0;                              // postings (sub-warp leaders)
+    unsigned long long n_post = 0, n_add = 0;   // postings scanned; shared-memory adds issued
     const int chunks = nb / (T * 4);  // <= 16 by construction (mask has 64 bits)
 
     // Warp 0 completes and merges the candidates a block deferred (few of them): one lane
@@ -520,7 +539,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                 bool ok = true;
                 if (lvl > 0) {
                     const double th = JT<W>::score_of_bits((uint32_t)((kth > fl ? kth : fl) >> 32));
-                    ok = JT<W>::exact_ok(v, Mr, p.ubound[(int64_t)lvl * p.u_stride + gid], th);
+                    ok = JT<W>::exact_ok(v, Mr, p.ubound[(int64_t)lvl * p.u_stride + gid], th, st.g);
                     if (ok) {   // Algorithm 4's dot over the unindexed features
                         const int64_t j0 = p.s_indptr[gid];
                         const int m = p.n_unidx[(int64_t)lvl * p.u_stride + gid];
@@ -702,6 +721,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                                            JT<W>::post_val(e[j], in ? m : (Mul)0));
                             if (COUNT) n_post += in && JT<W>::post_w(e[j]) != 0;   // padding has weight 0
                         }
+                        if (COUNT) n_add += V;
                     }
                 }
             }
@@ -869,7 +889,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                             sortbuf[atomicAdd(&st.cnt, 1)] = key;
                             n_push++;
                         }
-                    } else if (JT<W>::exact_ok(v, M, p.ubound[(int64_t)level * p.u_stride + gid], th)) {
+                    } else if (JT<W>::exact_ok(v, M, p.ubound[(int64_t)level * p.u_stride + gid], th, st.g)) {
                         const int slot = atomicAdd(&st.qcnt, 1);
                         if (slot >= CQ_CAP) break;   // queue full: keep this entry for the next pass
                         cq_gid[slot] = (uint32_t)gid;
@@ -947,15 +967,16 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     // counters
     if (p.touched || p.stats) {
         const bool t0 = tid == 0;
-        unsigned long long c[8] = {t0 ? st.n_steps : 0ull, n_cand, n_comp, n_push, t0 ? st.n_merges : 0ull,
-                                   t0 ? st.n_rounds : 0ull, n_resf, n_post};
+        unsigned long long c[KNN_STATS_LEN] = {t0 ? st.n_steps : 0ull, n_cand, n_comp, n_push,
+                                               t0 ? st.n_merges : 0ull, t0 ? st.n_rounds : 0ull, n_resf, n_post,
+                                               n_add};
 #pragma unroll
-        for (int j = 0; j < 8; j++)
+        for (int j = 0; j < KNN_STATS_LEN; j++)
             for (int o = 16; o > 0; o >>= 1) c[j] += __shfl_xor_sync(0xffffffffu, c[j], o);
         if (lane == 0) {
             if (p.touched && c[7]) atomicAdd(p.touched, c[7]);
             if (p.stats)
-                for (int j = 0; j < 8; j++)
+                for (int j = 0; j < KNN_STATS_LEN; j++)
                     if (c[j]) atomicAdd(p.stats + j, c[j]);
         }
     }
@@ -1456,8 +1477,9 @@ extern "C" knn_status knn_merge_topk(int32_t n_parts, const int32_t* const* part
 // Every GPU that loads this library holds that array until the process exits.
 //
 // Set-up: the first call on a device (with that device current) looks up the array's
-// device address with cudaGetSymbolAddress and caches it; that first call should be
-// made before any stream capture begins.  All calls share the one array and it keeps
+// device address with cudaGetSymbolAddress and caches it; make that first call before
+// any stream capture begins.  Every call also synchronises its stream (it reads R's
+// size back and, when validating, R's check record).  All calls share the one array and it keeps
 // the contents of the last call, so two calls whose work overlaps on the GPU (other
 // streams, other host threads) race on it; the check record is cleared on each call,
 // and every carried key is written before it is read.
@@ -1505,6 +1527,7 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     if (o.mode != KNN_MODE_IIIB && o.mode != KNN_MODE_IIB && o.mode != KNN_MODE_BF)
         return fail(KNN_EINVAL, "unknown mode");
     if (o.outputs_on_host) return fail(KNN_EINVAL, "knn_join_noalloc writes device outputs only");
+    if (R->n_rows < 0) return fail(KNN_EINVAL, "n_rows < 0");
     if (R->n_rows > 0 && (!out_ids || !out_scores)) return fail(KNN_EINVAL, "outputs are NULL");
     const size_t carry_cap = (KNN_NOALLOC_SCRATCH_BYTES - NOALLOC_HEADER) / sizeof(u64);
     if ((uint64_t)R->n_rows * (uint64_t)k > carry_cap)

@@ -233,9 +233,26 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const __
             if (done) break;
         }
         if (!done) s_fail = 1;
-        phase ^= 1u;
         __syncthreads();
-        if (s_fail) break;
+        if (s_fail) break;   // `phase` still names the step whose MMAs may be in flight
+        phase ^= 1u;
+    }
+    if (s_fail) {
+        // The MMAs of the step whose wait gave up may still be running, and the
+        // accumulator's tensor memory must not be released under them: wait for their
+        // commit once more, with the same bound.  If that wait gives up too, the
+        // columns stay allocated (the kernel returns without tcgen05.dealloc) and the
+        // error flag says so.
+        if (tid == 0) {
+            uint32_t done = 0;
+            for (long long spins = 0; spins < GEMM_WAIT_SPINS && !done; spins++)
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                    "selp.u32 %0, 1, 0, p;\n\t}"
+                    : "=r"(done) : "r"(mbar_a), "r"(phase) : "memory");
+            s_fail = done ? 1 : 2;
+        }
+        __syncthreads();
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!s_fail) {
@@ -262,11 +279,11 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const __
             }
         }
     } else if (tid == 0) {
-        atomicExch(&g_gemm_err, 1u);
+        atomicMax(&g_gemm_err, (unsigned)s_fail);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == 0 && s_fail != 2)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TN) : "memory");
 }
 
@@ -289,6 +306,9 @@ static knn_status gemm_check() {
     if (e) {
         const unsigned z = 0;
         KNN_CUDA_TRY(cudaMemcpyToSymbol(g_gemm_err, &z, sizeof(z)));
+        if (e >= 2)
+            return fail(KNN_ETIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs twice and left its "
+                                      "tensor memory allocated; treat this GPU context as unusable");
         return fail(KNN_ETIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs");
     }
     return KNN_OK;

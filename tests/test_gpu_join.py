@@ -168,6 +168,71 @@ def test_zipf_normalised_f32(knn, oracle_mod):
         compare.assert_close(R, S, list(range(R.n_rows)), ids, sc, eids, esc, what=f"zipf {mode}")
 
 
+def near_cut_f32(seed, k=20, dim=6000, base_nnz=1200, n_other=4000):
+    """S made of scaled copies of one long vector V (base_nnz features) and partial
+    copies, so that for ANY query r, score(r, c V) = c (r . V) orders the copies by c:
+      * k copies with c in [1, 1 + 1e-6]: the true top-k, all within 1e-6 of the cut;
+      * 30 copies with c in [1 - 2e-5, 1 - 1.2e-5]: the nearest non-neighbours, just
+        outside the 1e-5 tolerance (returning one instead of a true neighbour fails);
+      * n_other vectors holding 10-60 % of V's features at c in [0.3, 0.9] plus random
+        other features (scores below 0.9 of the cut).
+    The query rows overlap V heavily (800-1200 of its features plus others)."""
+    rng = np.random.default_rng(seed)
+    vd = np.sort(rng.choice(dim, base_nnz, replace=False))
+    vw = rng.lognormal(0.0, 1.0, base_nnz)
+    rows, tags = [], []
+    for c in 1.0 + rng.uniform(0.0, 1e-6, k):
+        rows.append(list(zip(vd.tolist(), (c * vw).tolist())))
+        tags.append("top")
+    for c in 1.0 - rng.uniform(1.2e-5, 2e-5, 30):
+        rows.append(list(zip(vd.tolist(), (c * vw).tolist())))
+        tags.append("near")
+    others = np.setdiff1d(np.arange(dim), vd)
+    for _ in range(n_other):
+        keep = rng.random(base_nnz) < rng.uniform(0.1, 0.6)
+        ex = rng.choice(others, size=int(rng.integers(0, 300)), replace=False)
+        c = rng.uniform(0.3, 0.9)
+        f = dict(zip(vd[keep].tolist(), (c * vw[keep]).tolist()))
+        f.update(zip(ex.tolist(), rng.lognormal(0.0, 1.0, ex.size).tolist()))
+        rows.append(sorted(f.items()))
+        tags.append("other")
+    order = rng.permutation(len(rows))
+    S = synth.from_rows([rows[i] for i in order], dim, np.float32)
+    tags = np.asarray(tags)[order]
+    qs = []
+    for _ in range(8):
+        keep = rng.random(base_nnz) < rng.uniform(0.65, 1.0)
+        ex = rng.choice(others, size=int(rng.integers(0, 200)), replace=False)
+        f = dict(zip(vd[keep].tolist(), rng.lognormal(0.0, 1.0, int(keep.sum())).tolist()))
+        f.update(zip(ex.tolist(), rng.lognormal(0.0, 1.0, ex.size).tolist()))
+        qs.append(sorted(f.items()))
+    return synth.from_rows(qs, dim, np.float32), S, tags
+
+
+@pytest.mark.parametrize("seed", [501, 502])
+def test_float_long_rows_neighbours_at_the_cut(knn, oracle_mod, seed):
+    """Long, heavily overlapping float rows (n = 800-1,200 shared features, so the fp32
+    sums carry up to ~1e-4 of worst-case rounding) with the true neighbours within 1e-6
+    of the k-th score and the nearest non-neighbours 1.2e-5 to 2e-5 below it: every
+    form of the join, including the Section 4.4 cut at its most aggressive margin,
+    must return exactly the k true neighbours."""
+    R, S, tags = near_cut_f32(seed)
+    k = 20
+    eids, esc, _ = oracle_mod.bf_join(R, S, k, threads=8)
+    assert all(set(tags[eids[i]]) == {"top"} for i in range(R.n_rows))   # the construction holds
+    idx = knn.knn_join_build_index(S, block_size=256, n_levels=32)
+    Rd = knn.DeviceCSR.from_host(R)
+    for kw in (dict(mode="iib"), dict(mode="iiib"), dict(mode="iiib", level_margin=1.0),
+               dict(mode="iiib", level_margin=1.0, s_groups=1), dict(mode="iiib", s_groups=4),
+               dict(mode="bf")):
+        ids, sc = knn.knn_join(idx, Rd, k, **kw)
+        ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+        compare.assert_close(R, S, list(range(R.n_rows)), ids, sc, eids, esc, what=f"near cut {kw}")
+        for i in range(R.n_rows):
+            assert set(ids[i].tolist()) == set(eids[i].tolist()), (kw, i)
+    idx.close()
+
+
 @pytest.mark.slow
 def test_config5_shaped_f32_sampled_rows(knn, oracle_mod):
     """The float scale-up's generator (Zipf ids over d = 50,000, power-law nnz up to
@@ -447,8 +512,10 @@ def test_config2_full_size_sampled_rows(knn, oracle_mod):
     ids, sc = knn.knn_join(idx, knn.DeviceCSR.from_host(R), k)
     torch.cuda.synchronize()
     ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
-    rows = np.random.default_rng(7).choice(R.n_rows, size=48, replace=False)
-    rows.sort()
+    # 2,000 rows spread over all of R (a stratified draw: one per 50-row stretch), bit-exact
+    rng = np.random.default_rng(7)
+    rows = np.arange(0, R.n_rows, R.n_rows // 2000)[:2000] + rng.integers(0, R.n_rows // 2000, size=2000)
+    assert rows.size == 2000 and rows.max() < R.n_rows
     Rs = R.take_rows(rows)
     eids, esc, _ = oracle_mod.iib_join(Rs, S, k, threads=0)
     compare.assert_exact(ids[rows], sc[rows], eids, esc, "config2 full size")

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 from paper_1011_2807_gb300 import synth
+import compare
 
 pytestmark = pytest.mark.gpu
 
@@ -76,22 +77,24 @@ def test_noalloc_equals_knn_join_on_two_calls(knn):
     idx.close()
 
 
-def test_noalloc_float_within_tolerance(knn):
+def test_noalloc_float_within_tolerance(knn, oracle_mod):
     import torch
     S = synth.uniform_f32(20000, 3000, 5, 40, 921)
     R = synth.uniform_f32(400, 3000, 5, 40, 922)
     idx = knn.knn_join_build_index(S, block_size=2048)
     Rd = knn.DeviceCSR.from_host(R)
     want_ids, want_sc = knn.knn_join(idx, Rd, 10, s_groups=1)
+    eids, esc, _ = oracle_mod.iib_join(R, S, 10, threads=8)
     for _ in range(2):
         ids = torch.empty((R.n_rows, 10), dtype=torch.int32, device="cuda")
         sc = torch.empty((R.n_rows, 10), dtype=torch.float32, device="cuda")
         knn.knn_join_noalloc(idx, Rd, 10, ids, sc)
         torch.cuda.synchronize()
-        # same method, summation order may differ: scores within the 1e-5 relative tolerance
+        # against the fp64 oracle: scores within 1e-5, ids equal but for boundary ties
+        compare.assert_close(R, S, list(range(R.n_rows)), ids.cpu().numpy(), sc.cpu().numpy(), eids, esc,
+                             what="knn_join_noalloc float")
+        # and against knn_join (the same method; summation order may differ)
         np.testing.assert_allclose(sc.cpu().numpy(), want_sc.cpu().numpy(), rtol=1e-5, atol=0)
-        same = (ids == want_ids).float().mean().item()
-        assert same > 0.99
     idx.close()
 
 
@@ -113,4 +116,10 @@ def test_noalloc_refuses_what_does_not_fit(knn):
     st = knn.lib().knn_join_noalloc(idx.handle, ctypes.byref(c), 5, ctypes.byref(opts),
                                     ids.data_ptr(), sc.data_ptr(), None)
     assert st == KNN_EINVAL and "device memory" in knn.knn_last_error()
+    # a negative row count is an invalid argument, as for knn_join
+    c = knn.binding._csr(Rd, [])
+    c.n_rows = -1
+    st = knn.lib().knn_join_noalloc(idx.handle, ctypes.byref(c), 5, ctypes.byref(opts),
+                                    ids.data_ptr(), sc.data_ptr(), None)
+    assert st == KNN_EINVAL and "n_rows" in knn.knn_last_error()
     idx.close()
