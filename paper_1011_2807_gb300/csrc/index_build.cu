@@ -198,51 +198,87 @@ __global__ void k_scatter(const int64_t* __restrict__ indptr, const int32_t* __r
     }
 }
 
-// Orders the postings of every bin inside each 32-chunk window of its list (half of
-// the join's work item) so that postings in the same slot j of the window's chunks fall
-// into different shared-memory banks (local id mod 32) wherever the bin's contents
-// allow: the 16 lanes of a sub-warp add slot j of 16 consecutive chunks of one window
-// with one instruction.  Only the order inside a bin changes, so every level's prefix
-// keeps the same postings.  One thread per (S block, d) list.
+// Orders the postings of every bin so that the join's add instructions hit different
+// shared-memory banks (local id mod 32) where the bin's contents allow.  The join adds
+// slot j of 32 consecutive chunks of its concatenated lists with one instruction, and
+// where a list sits in that concatenation depends on the query, so any two chunks of a
+// list fewer than 32 apart may share an instruction -- the nearer, the likelier.  Chunk
+// by chunk and slot by slot, the posting placed is the first of the bin's next
+// (up to) 32 chunks' worth whose bank has the least weight among the banks at the same
+// slot of the previous W - 1 chunks, a bank at distance t weighing W - t.  Padding
+// postings (weight 0, added nowhere that matters) take the least-weighted bank as their
+// local id.  Only the order inside a bin changes, so every level's prefix keeps the
+// same postings.  One thread per (S block, d) list.
 template <class Post, int V>
 __device__ __forceinline__ uint32_t post_bank(Post e);
 template <>
 __device__ __forceinline__ uint32_t post_bank<uint32_t, 4>(uint32_t e) { return e & 31u; }
 template <>
 __device__ __forceinline__ uint32_t post_bank<uint2, 2>(uint2 e) { return e.x & 31u; }
+template <class Post>
+__device__ __forceinline__ bool post_is_pad(Post e);
+template <>
+__device__ __forceinline__ bool post_is_pad<uint32_t>(uint32_t e) { return (e >> 24) == 0u; }
+template <>
+__device__ __forceinline__ bool post_is_pad<uint2>(uint2 e) { return e.y == 0u; }
+__device__ __forceinline__ uint32_t with_lid(uint32_t e, uint32_t lid) { return (e & 0xFFFF0000u) | lid; }
+__device__ __forceinline__ uint2 with_lid(uint2 e, uint32_t lid) { return make_uint2(lid, e.y); }
 
 template <class Post, int V>
 __global__ void k_arrange(const uint32_t* __restrict__ binoff, int64_t n_lists, int32_t n_levels,
                           Post* __restrict__ post) {
-    constexpr int ITEM = 32 * V;   // postings of one work item
+    constexpr int POOL = 32 * V;   // postings considered at once
+    constexpr int W = 24;          // chunks whose banks weigh on the next pick
     const int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (li >= n_lists) return;
     const uint32_t* bo = binoff + li * n_levels;
-    const uint32_t L0 = bo[0], L1 = bo[n_levels];   // the next list's start
-    Post buf[ITEM];
-    for (uint32_t a = L0; a < L1; a += ITEM) {
-        const uint32_t b = min(L1, a + (uint32_t)ITEM);
-        uint32_t used[V];
+    const uint32_t L0 = bo[0];
+    uint8_t ring[V][W];            // ring[j][c % W]: bank at slot j of chunk c (0xFF: none yet)
 #pragma unroll
-        for (int j = 0; j < V; j++) used[j] = 0u;
-        for (int t = 0; t < n_levels; t++) {
-            const uint32_t x = max(bo[t], a), y = min(bo[t + 1], b);
-            if (x >= y) continue;
-            int rem = (int)(y - x);
-            for (int i = 0; i < rem; i++) buf[i] = post[x + i];
-            for (uint32_t q = x; q < y; q++) {
-                uint32_t& u = used[q & (V - 1)];
+    for (int j = 0; j < V; j++)
+        for (int t = 0; t < W; t++) ring[j][t] = 0xFFu;
+    Post buf[POOL];
+    for (int t = 0; t < n_levels; t++) {
+        const uint32_t x = bo[t], y = bo[t + 1];
+        for (uint32_t a = x; a < y; a += POOL) {
+            const uint32_t b = min(y, a + (uint32_t)POOL);
+            int rem = (int)(b - a);
+            for (int i = 0; i < rem; i++) buf[i] = post[a + i];
+            for (uint32_t q = a; q < b; q++) {
+                const int j = (int)(q & (V - 1));
+                const uint32_t c = (q - L0) / V;   // chunk of the list (lists start on chunks)
+                uint32_t cost[32];
+#pragma unroll
+                for (int k = 0; k < 32; k++) cost[k] = 0u;
+                for (int e = 1; e < W; e++) {
+                    if (c < (uint32_t)e) break;
+                    const uint32_t bk = ring[j][(c - e) % W];
+                    if (bk != 0xFFu) cost[bk] += (uint32_t)(W - e);
+                }
                 int pick = 0;
-                for (int c = 0; c < rem; c++)
-                    if (!((u >> post_bank<Post, V>(buf[c])) & 1u)) {
-                        pick = c;
-                        break;
+                uint32_t best = 0xFFFFFFFFu;
+                for (int i = 0; i < rem; i++) {
+                    const uint32_t ci = post_is_pad(buf[i]) ? 0u : cost[post_bank<Post, V>(buf[i])];
+                    if (ci < best) {
+                        best = ci;
+                        pick = i;
+                        if (ci == 0u) break;
                     }
-                const Post e = buf[pick];
+                }
+                Post e = buf[pick];
                 buf[pick] = buf[rem - 1];
                 rem--;
+                if (post_is_pad(e)) {   // padding: the least-weighted bank as its local id
+                    uint32_t bk = 0, bc = cost[0];
+                    for (uint32_t k = 1; k < 32; k++)
+                        if (cost[k] < bc) {
+                            bc = cost[k];
+                            bk = k;
+                        }
+                    e = with_lid(e, bk);
+                }
                 post[q] = e;
-                u |= 1u << post_bank<Post, V>(e);
+                ring[j][c % W] = (uint8_t)post_bank<Post, V>(e);
             }
         }
     }

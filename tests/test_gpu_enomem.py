@@ -116,7 +116,7 @@ def test_join_enomem(knn, oracle_mod, kw):
 def test_batch_create_enomem(knn, oracle_mod):
     import torch
     S = synth.spectrum_u8(8000, 971, role="S")
-    idx = knn.knn_join_build_index(S, block_size=1024)
+    idx = knn.knn_join_build_index(S, block_size=2048)     # 4 S blocks, 2 per group
     Rs = [synth.spectrum_u8(n, 972 + i, role="R") for i, n in enumerate((40, 90))]
     jobs = [(idx, knn.DeviceCSR.from_host(R), k) for R, k in zip(Rs, (5, 9))]
     b, fails = fail_each_allocation(knn, lambda: knn.Batch(jobs, use_graph=False, blocks_per_group=2))
