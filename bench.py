@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-float", action="store_true", help="skip the float scale-up leg")
     ap.add_argument("--no-host-index", action="store_true", help="skip the host-resident index leg")
     ap.add_argument("--no-iib", action="store_true", help="skip the unrefined (IIB) comparison on the main workload")
+    ap.add_argument("--no-tiny", action="store_true", help="skip the tiny float workload leg")
     ap.add_argument("--no-learned-full-leg", action="store_true",
                     help="skip the learned-threshold workload at full size inside the main line")
     ap.add_argument("--no-float-full-leg", action="store_true",
@@ -146,20 +147,21 @@ def measured_sm_max_mhz():
         return 2070.0
 
 
-def profiled_traffic(kernel_src):
+def profiled_traffic(kernel_src, index_src):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on this
-    kernel source (sha256 recorded in the summary); else None."""
+    kernel and index-build source (sha256 of each recorded in the summary); else None."""
     path = os.path.join(ROOT, "profiles", "k_join_spectrum_config2.md")
     if not os.path.exists(path):
         return None, None
     txt = open(path).read()
     m = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"join_cu_sha256:\s*([0-9a-f]{64})", txt)
-    if not m or not h:
+    hi = re.search(r"index_build_cu_sha256:\s*([0-9a-f]{64})", txt)
+    if not m or not h or not hi:
         return None, None
-    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    if cur != h.group(1):
-        return None, "kernel changed since the ncu capture"
+    if hashlib.sha256(open(kernel_src, "rb").read()).hexdigest() != h.group(1) or \
+            hashlib.sha256(open(index_src, "rb").read()).hexdigest() != hi.group(1):
+        return None, "kernel or index build changed since the ncu capture"
     return float(m.group(1)), None
 
 
@@ -233,6 +235,50 @@ def cpu_oracle_rows_per_s(R, S, k, target_s, rows_lo=256, rows_hi=65536):
     oracle.iib_join(R.slice_rows(0, n), S, k, threads=0)
     dt = time.perf_counter() - t
     return n / dt, n, dt
+
+
+def cpu_bf_rows_per_s(R, S, k, target_s, rows_lo=16, rows_hi=4096):
+    """The CPU oracle's brute force (Algorithm 2, one thread) on a bounded sample of R
+    rows against the full S; returns (rows/s, rows, seconds)."""
+    import oracle
+    oracle.build()
+    n0 = min(rows_lo, R.n_rows)
+    t = time.perf_counter()
+    oracle.bf_join(R.slice_rows(0, n0), S, k, threads=1)
+    t0 = time.perf_counter() - t
+    n = int(min(rows_hi, R.n_rows, max(n0, n0 * target_s / max(t0, 1e-3))))
+    if n <= n0:
+        return n0 / t0, n0, t0
+    t = time.perf_counter()
+    oracle.bf_join(R.slice_rows(0, n), S, k, threads=1)
+    dt = time.perf_counter() - t
+    return n / dt, n, dt
+
+
+def cpu_pair(R, S, k, seconds):
+    """Both CPU oracles on bounded samples: the inverted-index join on all host cores and
+    the brute force on one core."""
+    v, n, dt = cpu_oracle_rows_per_s(R, S, k, seconds, rows_lo=16, rows_hi=65536)
+    b, nb, dtb = cpu_bf_rows_per_s(R, S, k, seconds, rows_lo=4)
+    return {"iib_all_cores_rows_per_s": v, "iib_rows": n, "iib_s": dt, "cores": os.cpu_count(),
+            "bf_one_core_rows_per_s": b, "bf_rows": nb, "bf_s": dtb}
+
+
+def tiny_leg(args, reps):
+    """The tiny plain join (|R| = 1,000, |S| = 10,000, d = 10,000, nnz U{20..100}, float32
+    uniform ids and weights, k = 10): GPU rows/s and both CPU oracles on bounded samples."""
+    import torch
+    import paper_1011_2807_gb300 as knn
+    from paper_1011_2807_gb300 import synth
+    R, S, k = synth.config1()
+    idx = knn.knn_join_build_index(S)
+    Rd = knn.DeviceCSR.from_host(R)
+    knn.knn_join(idx, Rd, k)
+    torch.cuda.synchronize()
+    ms = time_events(lambda: knn.knn_join(idx, Rd, k, skip_validation=True), reps)
+    idx.close()
+    return {"workload": "|R|=1,000, |S|=10,000, d=10,000, nnz U{20..100}, float32, k=10",
+            "gpu_rows_per_s": R.n_rows / (ms / 1e3), "gpu_ms": ms, "cpu": cpu_pair(R, S, k, 2.0)}
 
 
 # ----------------------------------------------------------------------------------
@@ -614,7 +660,8 @@ def run_ours(args):
     alg_bytes = bytes_post + bytes_r + bytes_out
     launches_per_step = max(1, launches // max(1, args.steps))   # k_join launches + R's row statistics
     join_launches = -(-info["n_blocks"] // max(1, args.blocks_per_launch))
-    traffic, traffic_note = profiled_traffic(os.path.join(ROOT, "paper_1011_2807_gb300", "csrc", "join.cu"))
+    traffic, traffic_note = profiled_traffic(os.path.join(ROOT, "paper_1011_2807_gb300", "csrc", "join.cu"),
+                                             os.path.join(ROOT, "paper_1011_2807_gb300", "csrc", "index_build.cu"))
     launch_s = kern_s / join_launches
     roofline = {"bound": "smem_atomic", "achieved": achieved_gadds, "peak": peak_gadds, "unit": "Gadd/s",
                 "frac": achieved_gadds / peak_gadds, "traffic": traffic,
@@ -671,6 +718,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_float_full_leg:
         ffull = float_full(args)
 
+    tiny = None
+    if rank == 0 and world == 1 and not args.no_tiny:
+        tiny = tiny_leg(args, reps=5)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, dt = cpu_oracle_rows_per_s(R, S, k, args.cpu_seconds)
@@ -678,6 +728,9 @@ def run_ours(args):
                "sample": f"first {n:,} of the {R.n_rows:,} R rows against all {S.n_rows:,} S vectors, "
                          f"{dt:.1f} s (Algorithm 3 in the block nested loop, OpenMP over rows, "
                          f"index build included)"}
+        b, nb, dtb = cpu_bf_rows_per_s(R, S, k, 5.0)
+        cpu["bf_one_core"] = {"value": b, "rows": nb, "s": dtb,
+                              "kind": "oracle brute force (Algorithm 2), one thread"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -696,6 +749,7 @@ def run_ours(args):
                 "e2e": e2e, "cpu_baseline": cpu, "learned_vs_plain": learned, "batched_vs_plain": batched,
                 "bf_vs_plain": bf, "float_scaleup": flt, "host_resident_index": host,
                 "iib_vs_iiib": iib, "learned_workload_full": lfull, "float_workload_full": ffull,
+                "tiny_workload": tiny,
                 "work_counters_per_step": work,
                 "kernel_ms_per_step": kern_ms}
         print(json.dumps(line), flush=True)
@@ -768,6 +822,8 @@ def learned_full(args):
         "batched": {"jobs": len(parts), "rows_per_s": n / (batched_ms / 1e3), "speedup": plain_ms / batched_ms,
                     "identical": bool(torch.equal(pids, bids) and torch.equal(psc, bsc))},
         "generate_s": gen_s}
+    if not args.no_cpu_baseline:
+        out["cpu"] = cpu_pair(E, S, k, 5.0)
     bt.close()
     model.close()
     idx.close()
@@ -861,6 +917,8 @@ def float_full(args):
         "batched": {"jobs": len(parts), "rows_per_s": n / (batched_ms / 1e3), "speedup": plain_ms / batched_ms,
                     "other_ids_vs_plain": boundary_ties(pids.cpu(), psc.cpu(), bids.cpu(), bsc.cpu())},
         "index_build_s": build_s, "generate_s": gen_s, "clocks": clk}
+    if not args.no_cpu_baseline:
+        out["cpu"] = cpu_pair(R, S, k, 5.0)
     b.close()
     model.close()
     idx.close()

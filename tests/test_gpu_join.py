@@ -209,6 +209,38 @@ def near_cut_f32(seed, k=20, dim=6000, base_nnz=1200, n_other=4000):
     return synth.from_rows(qs, dim, np.float32), S, tags
 
 
+def test_float_weights_across_binades(knn, oracle_mod):
+    """Float weights from 1e-12 to 1e12, a fifth of them just below a power of two (the
+    scan's rounded-up 17-bit weights then carry into the exponent), against the fp64
+    oracle in every form of the join."""
+    rng = np.random.default_rng(777)
+    dim = 3000
+
+    def draw(n, seed):
+        r = np.random.default_rng(seed)
+        rows = []
+        for _ in range(n):
+            m = int(r.integers(5, 120))
+            d = np.sort(r.choice(dim, m, replace=False))
+            w = 10.0 ** r.uniform(-12, 12, m)
+            edge = r.random(m) < 0.2
+            w[edge] = (2.0 - 2.0 ** -20) * 2.0 ** np.round(np.log2(w[edge]))
+            rows.append(list(zip(d.tolist(), w.astype(np.float32).tolist())))
+        return synth.from_rows(rows, dim, np.float32)
+
+    S, R = draw(5000, 778), draw(60, 779)
+    k = 12
+    eids, esc, _ = oracle_mod.bf_join(R, S, k, threads=8)
+    idx = knn.knn_join_build_index(S, block_size=1024)
+    Rd = knn.DeviceCSR.from_host(R)
+    for kw in (dict(mode="iib"), dict(mode="iiib"), dict(mode="iiib", level_margin=1.0, s_groups=1),
+               dict(mode="iiib", s_groups=3), dict(mode="bf")):
+        ids, sc = knn.knn_join(idx, Rd, k, **kw)
+        compare.assert_close(R, S, list(range(R.n_rows)), ids.cpu().numpy(), sc.cpu().numpy(), eids, esc,
+                             what=f"binades {kw}")
+    idx.close()
+
+
 @pytest.mark.parametrize("seed", [501, 502])
 def test_float_long_rows_neighbours_at_the_cut(knn, oracle_mod, seed):
     """Long, heavily overlapping float rows (n = 800-1,200 shared features, so the fp32
