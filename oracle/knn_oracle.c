@@ -116,7 +116,7 @@ int oracle_bf_join(const ocsr* R, const ocsr* S, int32_t k, int32_t nthreads,
     if (k < 1) return 1;
     int64_t steps_total = 0;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    omp_set_num_threads(nthreads > 0 ? nthreads : omp_get_num_procs());   // 0: every host core
 #endif
 #pragma omp parallel reduction(+ : steps_total)
     {
@@ -192,7 +192,7 @@ int oracle_iib_join(const ocsr* R, const ocsr* S, int32_t k, int64_t rblock, int
     if (rblock <= 0) rblock = R->n_rows > 0 ? R->n_rows : 1;
     if (sblock <= 0) sblock = S->n_rows > 0 ? S->n_rows : 1;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    omp_set_num_threads(nthreads > 0 ? nthreads : omp_get_num_procs());   // 0: every host core
 #endif
     ostats acc; memset(&acc, 0, sizeof(acc));
     inv_t I; inv_alloc(&I, S->dim, S->indptr[S->n_rows] - S->indptr[0]);
@@ -260,7 +260,7 @@ int oracle_iiib_join(const ocsr* R, const ocsr* S, int32_t k, int64_t rblock, in
     if (rblock <= 0) rblock = R->n_rows > 0 ? R->n_rows : 1;
     if (sblock <= 0) sblock = S->n_rows > 0 ? S->n_rows : 1;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    omp_set_num_threads(nthreads > 0 ? nthreads : omp_get_num_procs());   // 0: every host core
 #endif
     int32_t D = S->dim;
     ostats acc; memset(&acc, 0, sizeof(acc));

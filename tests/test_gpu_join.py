@@ -110,6 +110,17 @@ def test_threads(knn, oracle_mod, threads):
     compare.assert_exact(ids, sc, eids, esc, f"threads={threads}")
 
 
+@pytest.mark.parametrize("mode", ["iib", "iiib"])
+def test_largest_s_block(knn, oracle_mod, mode):
+    """S blocks of KNN_MAX_BLOCK = 32,768 vectors (a 128 KB accumulator, 1,024 threads,
+    one CTA per SM), three blocks with a ragged last one, bit-exact."""
+    S = synth.spectrum_u8(70000, 151, role="S")
+    R = synth.spectrum_u8(120, 152, role="R")
+    eids, esc, _ = oracle_mod.iib_join(R, S, 7, threads=8)
+    ids, sc = run(knn, S, R, 7, mode=mode, block_size=32768)
+    compare.assert_exact(ids, sc, eids, esc, f"block 32768 {mode}")
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_random_small_dims_many_ties(knn, oracle_mod, seed):
     # few dimensions and weights in {1,2}: scores tie everywhere
