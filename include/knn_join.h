@@ -182,6 +182,12 @@ typedef struct {
                                    every launch covers all rows (0 = as many as keep one
                                    launch's postings within ~48 MB, so that they stay in
                                    L2 while every row reads them; at most 16)              */
+    int32_t no_fixed_point;     /* float32 only.  0 (default): from the second S-block
+                                   launch on, a row whose current k-th score is large
+                                   enough sums its scan in fixed point (power-of-two scale
+                                   under |r| max|s|; the absolute error stays below 2^-18
+                                   of that k-th score, 4e-6 relative); 1: every scan sums
+                                   in fp32                                                 */
 } knn_join_opts;
 
 /* Top-k of the union of several S shards (no paper counterpart: the exchange step of
@@ -211,7 +217,9 @@ knn_status knn_merge_topk(int32_t n_parts, const int32_t* const* part_ids, const
 #define KNN_STAT_SHARED_ADDS 8      /* shared-memory adds issued by the scan: every posting
                                        slot of the 16-byte chunks read, the zero-weight
                                        padding and the slots past a level's prefix included */
-#define KNN_STATS_LEN 9
+#define KNN_STAT_FIXED_POINT_ROWS 9 /* (row, S-block launch) pairs whose scan summed in fixed
+                                       point (float joins; see no_fixed_point)              */
+#define KNN_STATS_LEN 10
 
 /* Exact top-k of every row of R against the indexed S.
  *   index       built by knn_join_build_index (same dim and dtype as R).

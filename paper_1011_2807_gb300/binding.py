@@ -63,10 +63,11 @@ class _JoinOpts(ctypes.Structure):
                 ("init_threshold", ctypes.c_void_p), ("n_found", ctypes.c_void_p),
                 ("postings_scanned", ctypes.c_void_p), ("outputs_on_host", ctypes.c_int32),
                 ("skip_validation", ctypes.c_int32), ("level_margin", ctypes.c_float),
-                ("stats", ctypes.c_void_p), ("blocks_per_launch", ctypes.c_int32)]
+                ("stats", ctypes.c_void_p), ("blocks_per_launch", ctypes.c_int32),
+                ("no_fixed_point", ctypes.c_int32)]
 
 KNN_STATS = ("block_steps", "candidates", "completed", "pushed", "merges", "rounds",
-             "residual_features", "postings", "shared_adds")
+             "residual_features", "postings", "shared_adds", "fixed_point_rows")
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -268,7 +269,8 @@ def knn_join(index: Index, R, k: int, *, mode: str = "iiib", threads: int = 0, s
              init_threshold: torch.Tensor | None = None, n_found: torch.Tensor | None = None,
              postings_scanned: torch.Tensor | None = None, out_ids=None, out_scores=None,
              outputs_on_host: bool = False, skip_validation: bool = False, level_margin: float = 0.0,
-             stats: torch.Tensor | None = None, blocks_per_launch: int = 0, stream=None):
+             stats: torch.Tensor | None = None, blocks_per_launch: int = 0, fixed_point: bool = True,
+             stream=None):
     """Exact top-k of every row of R; returns (ids, scores).
 
     Device outputs are torch tensors on the current device unless ``out_ids`` /
@@ -290,7 +292,7 @@ def knn_join(index: Index, R, k: int, *, mode: str = "iiib", threads: int = 0, s
     opts = _JoinOpts(_mode(mode), int(threads), int(s_groups),
                      _ptr(init_threshold), _ptr(n_found), _ptr(postings_scanned),
                      int(bool(outputs_on_host)), int(bool(skip_validation)), float(level_margin),
-                     _ptr(stats), int(blocks_per_launch))
+                     _ptr(stats), int(blocks_per_launch), int(not fixed_point))
     ip = out_ids.ctypes.data if isinstance(out_ids, np.ndarray) else out_ids.data_ptr()
     sp = out_scores.ctypes.data if isinstance(out_scores, np.ndarray) else out_scores.data_ptr()
     _check(L, L.knn_join(index.handle, ctypes.byref(c), int(k), ctypes.byref(opts), ip, sp,

@@ -90,6 +90,7 @@ struct DevCSR {
     int32_t max_row_nnz = 0;
     double max_w = 0.0;        // largest weight
     double max_row_sum = 0.0;  // largest sum of a row's weights
+    double max_row_norm = 0.0; // largest L2 norm of a row (rounded up)
 };
 
 // Uploads (if on host) and validates a CSR; buffers it allocates go to `bufs`.
@@ -112,7 +113,7 @@ struct knn_index {
     int32_t dim = 0, block_size = 0, n_blocks = 0, n_levels = 0, block_shift = 0;
     knn_dtype dtype = KNN_U8;
     int32_t max_row_nnz = 0;
-    double max_w = 0.0, max_row_sum = 0.0;
+    double max_w = 0.0, max_row_sum = 0.0, max_row_norm = 0.0;
     float levels[KNN_MAX_LEVELS] = {};  // ladder of bound thresholds, levels[0] == 0
     // device arrays
     uint32_t* binoff = nullptr;  // [n_blocks * dim * n_levels + 1] posting-bin offsets

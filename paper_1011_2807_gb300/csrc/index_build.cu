@@ -329,6 +329,7 @@ extern "C" knn_status knn_join_build_index(const knn_csr* S, const knn_build_opt
     ix->max_row_nnz = s.max_row_nnz;
     ix->max_w = s.max_w;
     ix->max_row_sum = s.max_row_sum;
+    ix->max_row_norm = s.max_row_norm;
     int32_t bs = o.block_size;
     if (bs == 0) {
         bs = 16384;

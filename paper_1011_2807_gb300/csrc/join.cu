@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -52,6 +53,7 @@ struct JT<uint8_t> {
     using Acc = int32_t;
     using Post = uint32_t;
     static constexpr int PER_VEC = 4;  // postings per 16-byte load
+    static constexpr bool FIXED_OK = false;   // scores are integers already
     __device__ static uint32_t score_bits(int32_t v) { return (uint32_t)v; }
     __device__ static double score_of_bits(uint32_t b) { return (double)b; }
     __device__ static int32_t value_of_bits(uint32_t b) { return (int32_t)b; }
@@ -124,6 +126,7 @@ struct JT<float> {
     using Acc = float;
     using Post = uint2;
     static constexpr int PER_VEC = 2;
+    static constexpr bool FIXED_OK = true;    // the scan may accumulate in fixed point
     __device__ static uint32_t score_bits(float v) { return __float_as_uint(v); }
     __device__ static double score_of_bits(uint32_t b) { return (double)__uint_as_float(b); }
     __device__ static float value_of_bits(uint32_t b) { return __uint_as_float(b); }
@@ -211,6 +214,9 @@ struct JoinParams {
     const uint16_t* n_unidx;
     const uint32_t* ubound;
     int64_t u_stride;   // elements between levels of n_unidx / ubound (|S|, or a staged slice's)
+    float s_maxnorm;    // largest L2 norm of an S vector, rounded up (float scores: fixed-point scale)
+    uint8_t* fx_done;   // float, S-block-synchronous: per row, 1 if the fixed-point launch of this
+                        // S range joined it (the fp32 launch then skips it), else 0
     float levels[KNN_MAX_LEVELS];
     int32_t k, groups, blocks_per_group, iiib, max_r_nnz;
     int32_t bf;         // brute force: every s scored in full (Algorithm 2), no posting scan
@@ -285,6 +291,9 @@ struct CtaState {
     u64 kth;        // current k-th key (0 while fewer than k)
     double M;       // largest weight of r
     double g;       // relative rounding allowance of a completed score (0 for integers)
+    int fx;         // float scores: this row accumulates the scan in fixed point (fx_decide)
+    float fx_scale, fx_inv;   // the fixed-point scale (a power of two) and its inverse
+    double fx_rsq;  // |r|^2
     double lb;      // residual bound of the current level (0 at level 0)
     float cmin_f;   // smallest partial score worth a look in this block (as float/int)
     int32_t cmin_i;
@@ -430,12 +439,50 @@ __device__ __forceinline__ void prepare_block_warp(const JoinParams& p, const in
     if (lane == 0) ipre[rn] = carry;
 }
 
-template <class W, bool COUNT, bool BF>
+// Float rows may accumulate the scan in fixed point: each product r[d] w times a
+// power-of-two scale, rounded to an integer, added with an integer shared-memory
+// atomic (2.5x the rate of the float one on this GPU), and integer sums do not depend
+// on the order of the adds.  The scale keeps every partial below 2^30 -- a score, and any
+// one product, is at most |r| max|s| (Cauchy-Schwarz) -- so a partial converted back is
+// off by at most n / (2 scale) (n = nnz(r) rounded terms) besides fp32's relative
+// rounding of the products and of the conversion.  A row takes this path only when
+// that absolute error is at most 2^-18 of its current k-th score, which only grows, so
+// every score it returns keeps the error below 4e-6 relative; that needs the k-th
+// score carried in from earlier S blocks.  Nothing else changes: the kernel ranks the
+// converted partials like fp32 ones, and every bound of the cut is stated in terms of
+// the computed partial.
+template <class S>
+__device__ void fx_decide(const JoinParams& p, S& st, int rn) {
+    st.fx = 0;
+    st.fx_scale = 1.0f;
+    st.fx_inv = 1.0f;
+    if (!st.kth || !(p.s_maxnorm >= 1e-18f) || !(st.fx_rsq > 0.0) || !(st.fx_rsq < 1e300)) return;
+    const double th = (double)__uint_as_float((uint32_t)(st.kth >> 32));
+    const double ub = sqrt(st.fx_rsq) * (1.0 + 1e-9) * (double)p.s_maxnorm;
+    int e;
+    frexp(ub, &e);                   // ub < 2^e
+    const int es = 30 - e;           // scale 2^es: ub * scale < 2^30
+    if (es > 100 || es < -100) return;
+    const double scale = ldexp(1.0, es);
+    if (0.5 * (double)rn / scale > th * (1.0 / 262144.0)) return;
+    st.fx = 1;
+    st.fx_scale = (float)scale;
+    st.fx_inv = (float)(1.0 / scale);
+}
+
+template <class W, bool COUNT, bool BF, bool FX>
 __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row, const int g, const int b0,
                                          const int b1, const bool carry_in, const int out_mode,
                                          unsigned char* smem) {
     using Acc = typename JT<W>::Acc;
     using Post = typename JT<W>::Post;
+    // FX: the fixed-point launch of a float join (rows whose precision test fails are left
+    // to the fp32 launch that follows); otherwise the fp32 (or integer) join, which skips
+    // rows the fixed-point launch already joined
+    constexpr bool FXABLE = JT<W>::FIXED_OK && !BF && FX;
+    if constexpr (JT<W>::FIXED_OK && !BF && !FX) {
+        if (p.fx_done && p.fx_done[row]) return;
+    }
     __shared__ CtaState st;
     __shared__ uint32_t red_m[32];
     __shared__ unsigned long long red_u[32];
@@ -462,14 +509,20 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
 
     // load r (ascending d) and its largest weight
     uint32_t mloc = 0u;   // as score bits: weights are > 0, so the bits order like the values
+    float rsq = 0.0f;     // sum of squared weights (float rows: the fixed-point scale)
     for (int i = tid; i < rn; i += T) {
         rf_d[i] = p.r_idx[ra + i];
         Acc w = (Acc)((const W*)p.r_val)[ra + i];
         rf_w[i] = w;
         mloc = max(mloc, JT<W>::score_bits(w));
+        if (FXABLE) rsq = fmaf((float)w, (float)w, rsq);
     }
     mloc = __reduce_max_sync(0xffffffffu, mloc);
     if (lane == 0) red_m[warp] = mloc;
+    if (FXABLE) {
+        for (int o = 16; o > 0; o >>= 1) rsq += __shfl_xor_sync(0xffffffffu, rsq, o);
+        if (lane == 0) red_u[warp] = (unsigned long long)__float_as_uint(rsq);
+    }
     // clear the accumulator (and the dense copy of r)
     for (int i = tid * 4; i < nb; i += T * 4) *(int4*)(acc + i) = make_int4(0, 0, 0, 0);
     if (rden) {
@@ -488,9 +541,15 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
             JT<W>::need(st, lane) = JT<W>::level_need(lb, p.level_margin);
             JT<W>::lbu(st, lane) = JT<W>::bound_up(lb);
         }
+        if (FXABLE && lane == 0) {
+            double q = 0.0;
+            for (int w = 0; w < nwarps; w++) q += (double)__uint_as_float((uint32_t)red_u[w]);
+            st.fx_rsq = q * (1.0 + (double)(rn + 32) * (1.0 / 8388608.0));   // fp32 sums, rounded up
+        }
         if (lane == 0) {
             st.M = m;
             st.g = g;
+            st.fx = 0;
             st.size = 0;
             st.cnt = 0;
             st.kth = 0ull;
@@ -511,7 +570,12 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
             st.kth = n == p.k ? topk[p.k - 1] : 0ull;
         }
     }
+    if (FXABLE && tid == 0) {
+        fx_decide(p, st, rn);
+        p.fx_done[row] = (uint8_t)st.fx;
+    }
     __syncthreads();
+    if (FXABLE && !st.fx) return;   // the fp32 launch joins this row over the same S blocks
 
     uint32_t n_cand = 0, n_comp = 0, n_push = 0, n_resf = 0;   // this thread's counters
     unsigned long long n_post = 0, n_add = 0;   // postings scanned; shared-memory adds issued
@@ -696,41 +760,52 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                 li = lo;
             }
             using Mul = typename JT<W>::Mul;
-            for (uint32_t I = I0; I < I1; I++) {
-                while (ipre[li + 1] <= I) li++;
-                const uint32_t en = lend[li];
-                const Mul m = JT<W>::scan_mul(rf_w[li]);
-                const uint32_t p0 = lbeg[li] + (I - ipre[li]) * (CH * V) + (uint32_t)sl * V;   // this lane's first posting
-                const uint4* src = (const uint4*)(post + p0);
-                uint4 v[U];
+            // FX: the row accumulates rounded, scaled products in integers (fx_decide)
+            auto scan_items = [&](auto fx_tag, const float fxs) {
+                constexpr bool FX = decltype(fx_tag)::value;
+                for (uint32_t I = I0; I < I1; I++) {
+                    while (ipre[li + 1] <= I) li++;
+                    const uint32_t en = lend[li];
+                    const Mul m = JT<W>::scan_mul(FX ? rf_w[li] * fxs : rf_w[li]);
+                    const uint32_t p0 = lbeg[li] + (I - ipre[li]) * (CH * V) + (uint32_t)sl * V;   // this lane's first posting
+                    const uint4* src = (const uint4*)(post + p0);
+                    uint4 v[U];
 #pragma unroll
-                for (int u = 0; u < U; u++)
-                    if (p0 + (uint32_t)(G * u * V) < en) v[u] = src[G * u];
+                    for (int u = 0; u < U; u++)
+                        if (p0 + (uint32_t)(G * u * V) < en) v[u] = src[G * u];
 #pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const uint32_t q = p0 + (uint32_t)(G * u * V);
-                    if (q < en) {
-                        // postings of the chunk past the prefix end (level > 0) belong to the
-                        // same list: they are added with weight 0 rather than branched around
-                        const Post* e = (const Post*)&v[u];
-                        const uint32_t nv = en - q;
+                    for (int u = 0; u < U; u++) {
+                        const uint32_t q = p0 + (uint32_t)(G * u * V);
+                        if (q < en) {
+                            // postings of the chunk past the prefix end (level > 0) belong to the
+                            // same list: they are added with weight 0 rather than branched around
+                            const Post* e = (const Post*)&v[u];
+                            const uint32_t nv = en - q;
 #pragma unroll
-                        for (int j = 0; j < V; j++) {
-                            const bool in = j == 0 || (uint32_t)j < nv;
-                            red_add_shared(acc_s + 4u * (uint32_t)JT<W>::post_lid(e[j]),
-                                           JT<W>::post_val(e[j], in ? m : (Mul)0));
-                            if (COUNT) n_post += in && JT<W>::post_w(e[j]) != 0;   // padding has weight 0
+                            for (int j = 0; j < V; j++) {
+                                const bool in = j == 0 || (uint32_t)j < nv;
+                                const uint32_t addr = acc_s + 4u * (uint32_t)JT<W>::post_lid(e[j]);
+                                if constexpr (FX)
+                                    red_add_shared(addr, (int32_t)__float2int_rn(JT<W>::post_val(e[j], in ? m : (Mul)0)));
+                                else
+                                    red_add_shared(addr, JT<W>::post_val(e[j], in ? m : (Mul)0));
+                                if (COUNT) n_post += in && JT<W>::post_w(e[j]) != 0;   // padding has weight 0
+                            }
+                            if (COUNT) n_add += V;
                         }
-                        if (COUNT) n_add += V;
                     }
                 }
-            }
+            };
+            if constexpr (FXABLE) scan_items(std::true_type{}, st.fx_scale);
+            else scan_items(std::false_type{}, 1.0f);
         }
         __syncthreads();
         // ---- 3. select ----
         const double M = st.M;
         const double lb = st.lb;
         const Acc cmin = JT<W>::get_cmin(st);   // > 0
+        constexpr bool fxrow = FXABLE;   // every row of the fixed-point launch
+        const float fxinv = st.fx_inv;
         const int64_t gbase = (int64_t)b << p.block_shift;
         unsigned long long mask = 0ull;
         int mycount = 0;
@@ -738,6 +813,10 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         for (int c = 0; c < chunks; c++) {
             int lid0 = c * T * 4 + tid * 4;
             int4 raw = ld_shared_v4(acc_s + 4u * lid0);
+            if (FXABLE && fxrow) {   // fixed-point partials back to floats (0 stays 0)
+                raw = make_int4(__float_as_int(__int2float_rn(raw.x) * fxinv), __float_as_int(__int2float_rn(raw.y) * fxinv),
+                                __float_as_int(__int2float_rn(raw.z) * fxinv), __float_as_int(__int2float_rn(raw.w) * fxinv));
+            }
             Acc* v = (Acc*)&raw;
             if (v[0] < cmin && v[1] < cmin && v[2] < cmin && v[3] < cmin) {
                 st_shared_v4(acc_s + 4u * lid0, make_int4(0, 0, 0, 0));
@@ -969,7 +1048,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         const bool t0 = tid == 0;
         unsigned long long c[KNN_STATS_LEN] = {t0 ? st.n_steps : 0ull, n_cand, n_comp, n_push,
                                                t0 ? st.n_merges : 0ull, t0 ? st.n_rounds : 0ull, n_resf, n_post,
-                                               n_add};
+                                               n_add, (t0 && FXABLE) ? 1ull : 0ull};
 #pragma unroll
         for (int j = 0; j < KNN_STATS_LEN; j++)
             for (int o = 16; o > 0; o >>= 1) c[j] += __shfl_xor_sync(0xffffffffu, c[j], o);
@@ -982,29 +1061,31 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
     }
 }
 
-template <class W, bool COUNT, bool BF>
+template <class W, bool COUNT, bool BF, bool FX>
 __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int64_t row = blockIdx.x / p.groups;
     const int g = blockIdx.x - (int)(row * p.groups);
     if (p.groups == 1)
-        join_row<W, COUNT, BF>(p, row, 0, p.block_begin, p.block_end, p.carry_in != 0,
-                           p.carry_out ? OUT_CARRY : OUT_FINAL, smem);
+        join_row<W, COUNT, BF, FX>(p, row, 0, p.block_begin, p.block_end, p.carry_in != 0,
+                                   p.carry_out ? OUT_CARRY : OUT_FINAL, smem);
     else
-        join_row<W, COUNT, BF>(p, row, g, g * p.blocks_per_group, min(p.n_blocks, (g + 1) * p.blocks_per_group), false,
-                           OUT_GROUP, smem);
+        join_row<W, COUNT, BF, FX>(p, row, g, g * p.blocks_per_group,
+                                   min(p.n_blocks, (g + 1) * p.blocks_per_group), false, OUT_GROUP, smem);
 }
 
 // The posting count (stats, eq. 4 checks) costs a compare per posting, so it is
-// compiled into a separate instance that runs only when a counter is requested.
+// compiled into a separate instance that runs only when a counter is requested; the
+// fixed-point launch of float joins (fx) is an instance of its own as well.
 using JoinKernel = void (*)(JoinParams);
-static JoinKernel join_kernel(knn_dtype dt, bool count, bool bf) {
+static JoinKernel join_kernel(knn_dtype dt, bool count, bool bf, bool fx = false) {
     if (bf) {
-        if (dt == KNN_U8) return count ? k_join<uint8_t, true, true> : k_join<uint8_t, false, true>;
-        return count ? k_join<float, true, true> : k_join<float, false, true>;
+        if (dt == KNN_U8) return count ? k_join<uint8_t, true, true, false> : k_join<uint8_t, false, true, false>;
+        return count ? k_join<float, true, true, false> : k_join<float, false, true, false>;
     }
-    if (dt == KNN_U8) return count ? k_join<uint8_t, true, false> : k_join<uint8_t, false, false>;
-    return count ? k_join<float, true, false> : k_join<float, false, false>;
+    if (dt == KNN_U8) return count ? k_join<uint8_t, true, false, false> : k_join<uint8_t, false, false, false>;
+    if (fx) return count ? k_join<float, true, false, true> : k_join<float, false, false, true>;
+    return count ? k_join<float, true, false, false> : k_join<float, false, false, false>;
 }
 
 
@@ -1071,7 +1152,7 @@ __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ B
         __syncthreads();
         if (g > 0 && !s_ok) continue;
         const bool last = g == J.groups - 1;
-        join_row<W, COUNT, false>(J, row, g, g * J.blocks_per_group, min(J.n_blocks, (g + 1) * J.blocks_per_group),
+        join_row<W, COUNT, false, false>(J, row, g, g * J.blocks_per_group, min(J.n_blocks, (g + 1) * J.blocks_per_group),
                            g > 0, last ? OUT_FINAL : OUT_CARRY, smem);
         if (!last && !no_publish) {   // publish: the carried keys are in global memory before the flag
             __syncthreads();
@@ -1184,6 +1265,15 @@ static int default_blocks_per_launch(const knn_index* ix) {
     const double per_block = (double)ix->n_postings * post_bytes / (double)std::max(1, ix->n_blocks);
     const int b = per_block > 0.0 ? (int)std::min(16.0, 48.0e6 / per_block) : 16;
     return std::max(1, b);
+}
+
+// the largest L2 norm of an S vector as a float not below it (0 when unknown or not finite)
+static float maxnorm_up(const knn_index* ix) {
+    const double v = ix->max_row_norm;
+    if (!(v > 0.0) || v > 1e37) return 0.0f;
+    float f = (float)v;
+    if ((double)f < v) f = std::nextafter(f, 3.4e38f);
+    return f;
 }
 
 static SliceRange slice_of(const knn_index* ix, int li, int per_launch) {
@@ -1364,6 +1454,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     p.n_unidx = ix->n_unidx;
     p.ubound = ix->ubound;
     p.u_stride = ix->n_rows;
+    p.s_maxnorm = maxnorm_up(ix);
     memcpy(p.levels, ix->levels, sizeof(p.levels));
     p.k = k;
     p.groups = groups;
@@ -1401,6 +1492,19 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
         KNN_TRY(stage_setup(ix, per_launch, n_launch, tmp, staged));
         KNN_TRY(stage_copy(ix, 0, per_launch, false, staged));
     }
+    // Float joins over several S-block launches: from the second launch on, the rows whose
+    // carried k-th score proves the fixed-point scan precise enough (fx_decide) are joined
+    // by the fixed-point instance, and the fp32 instance then joins the rest of the rows
+    // over the same S blocks (it skips those marked done).
+    const bool use_fx = ix->dtype == KNN_F32 && !p.bf && groups == 1 && n_launch > 1 && p.s_maxnorm > 0.0f &&
+                        !o.no_fixed_point;
+    JoinKernel kern_fx = nullptr;
+    uint8_t* fx_done = nullptr;
+    if (use_fx) {
+        kern_fx = join_kernel(ix->dtype, p.touched || p.stats, false, true);
+        KNN_CUDA_TRY(cudaFuncSetAttribute(kern_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+        KNN_TRY(tmp.get(&fx_done, (size_t)r.n_rows));
+    }
     for (int li = 0; li < n_launch; li++) {
         p.block_begin = li * per_launch;
         p.block_end = std::min(ix->n_blocks, (li + 1) * per_launch);
@@ -1411,6 +1515,12 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
             if (li + 1 < n_launch) KNN_TRY(stage_copy(ix, li + 1, per_launch, li >= 1, staged));
             KNN_CUDA_TRY(cudaStreamWaitEvent(stream, staged.copied[li & 1], 0));
             stage_params(ix, li, per_launch, staged, p);
+        }
+        p.fx_done = use_fx && li > 0 ? fx_done : nullptr;
+        if (p.fx_done) {
+            kern_fx<<<(unsigned)grid, T, L.total, stream>>>(p);
+            KNN_CUDA_TRY(cudaGetLastError());
+            count_launch();
         }
         kern<<<(unsigned)grid, T, L.total, stream>>>(p);
         KNN_CUDA_TRY(cudaGetLastError());
@@ -1587,6 +1697,7 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     p.n_unidx = ix->n_unidx;
     p.ubound = ix->ubound;
     p.u_stride = ix->n_rows;
+    p.s_maxnorm = maxnorm_up(ix);
     memcpy(p.levels, ix->levels, sizeof(p.levels));
     p.k = k;
     p.groups = 1;   // one group per row: the only schedule whose scratch is the carry buffer
@@ -1769,6 +1880,7 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
         p.n_unidx = ix->n_unidx;
         p.ubound = ix->ubound;
         p.u_stride = ix->n_rows;
+        p.s_maxnorm = maxnorm_up(ix);
         memcpy(p.levels, ix->levels, sizeof(p.levels));
         p.k = jb.k;
         p.groups = groups;

@@ -94,6 +94,7 @@ struct CsrCheck {
     int32_t max_nnz;
     uint32_t max_w_bits;                // float bits of the largest weight
     unsigned long long max_sum_bits;   // double bits of the largest row sum
+    unsigned long long max_sq_bits;    // double bits of the largest sum of squared weights
 };
 
 __global__ void k_check_indptr(const int64_t* __restrict__ indptr, int64_t n, int64_t nnz,
@@ -126,7 +127,7 @@ __global__ void k_check_rows(const int64_t* __restrict__ indptr, const int32_t* 
         int64_t a = indptr[row], b = indptr[row + 1];
         uint32_t flags = 0;
         float wmax = 0.0f;
-        double sum = 0.0;
+        double sum = 0.0, sq = 0.0;
         for (int64_t j = a + lane; j < b; j += 32) {
             int32_t d = idx[j];
             if (d < 0 || d >= dim) flags |= BAD_DIM;
@@ -136,11 +137,13 @@ __global__ void k_check_rows(const int64_t* __restrict__ indptr, const int32_t* 
             float wf = (float)w;
             if (wf > wmax) wmax = wf;
             sum += (double)wf;
+            sq += (double)wf * (double)wf;
         }
         for (int o = 16; o > 0; o >>= 1) {
             flags |= __shfl_xor_sync(0xffffffffu, flags, o);
             wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
             sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            sq += __shfl_xor_sync(0xffffffffu, sq, o);
         }
         if (lane == 0) {
             if (flags) atomicOr(&out->flags, flags);
@@ -148,6 +151,8 @@ __global__ void k_check_rows(const int64_t* __restrict__ indptr, const int32_t* 
             if (wmax == wmax && wmax > 0.0f) atomicMax(&out->max_w_bits, __float_as_uint(wmax));
             if (sum > 0.0 && sum < 1e300)
                 atomicMax(&out->max_sum_bits, (unsigned long long)__double_as_longlong(sum));
+            if (sq > 0.0 && sq < 1e300)
+                atomicMax(&out->max_sq_bits, (unsigned long long)__double_as_longlong(sq));
         }
     }
 }
@@ -242,6 +247,9 @@ knn_status prepare_csr(const knn_csr* in, cudaStream_t stream, Buffers& bufs, bo
     double ms;
     memcpy(&ms, &h.max_sum_bits, 8);
     out->max_row_sum = ms;
+    double mq;
+    memcpy(&mq, &h.max_sq_bits, 8);
+    out->max_row_norm = std::sqrt(mq) * (1.0 + 1e-9);   // rounded up: a bound for every row
     return KNN_OK;
 }
 
@@ -310,6 +318,9 @@ knn_status check_device_csr_into(const knn_csr* in, void* scratch, bool validate
     double ms;
     memcpy(&ms, &h.max_sum_bits, 8);
     out->max_row_sum = ms;
+    double mq;
+    memcpy(&mq, &h.max_sq_bits, 8);
+    out->max_row_norm = std::sqrt(mq) * (1.0 + 1e-9);   // rounded up: a bound for every row
     return KNN_OK;
 }
 

@@ -276,6 +276,38 @@ def test_float_long_rows_neighbours_at_the_cut(knn, oracle_mod, seed):
     idx.close()
 
 
+@pytest.mark.parametrize("mode", ["iib", "iiib"])
+def test_float_fixed_point_scan(knn, oracle_mod, mode):
+    """Float joins over several S-block launches: from the second launch on, rows whose
+    carried k-th score allows it sum their scan in fixed point.  Both sums, and the
+    default that mixes them, agree with the fp64 oracle within the float tolerance, the
+    fixed-point path ran for most (row, launch) pairs, and every row was joined once per
+    launch (the fp32 launch skips the rows the fixed-point launch took)."""
+    import torch
+    from paper_1011_2807_gb300.binding import KNN_STATS
+    S = synth.zipf_f32(12000, 931, dim=3000, nnz_hi=400)
+    R = synth.zipf_f32(150, 932, dim=3000, nnz_hi=400)
+    k = 15
+    eids, esc, _ = oracle_mod.bf_join(R, S, k, threads=8)
+    idx = knn.knn_join_build_index(S, block_size=512)          # 24 S blocks
+    Rd = knn.DeviceCSR.from_host(R)
+    n_launch = -(-idx.info()["n_blocks"] // 3)
+    for fixed in (True, False):
+        st = torch.zeros(len(KNN_STATS), dtype=torch.int64, device="cuda")
+        ids, sc = knn.knn_join(idx, Rd, k, mode=mode, s_groups=1, blocks_per_launch=3, fixed_point=fixed,
+                               stats=st)
+        compare.assert_close(R, S, list(range(R.n_rows)), ids.cpu().numpy(), sc.cpu().numpy(), eids, esc,
+                             what=f"fixed_point={fixed} {mode}")
+        w = dict(zip(KNN_STATS, st.cpu().tolist()))
+        nonempty = int((np.diff(R.indptr) > 0).sum())
+        assert w["block_steps"] == nonempty * idx.info()["n_blocks"]       # each row once per S block
+        if fixed:
+            assert w["fixed_point_rows"] > 0.5 * nonempty * (n_launch - 1), w
+        else:
+            assert w["fixed_point_rows"] == 0
+    idx.close()
+
+
 @pytest.mark.slow
 def test_config5_shaped_f32_sampled_rows(knn, oracle_mod):
     """The float scale-up's generator (Zipf ids over d = 50,000, power-law nnz up to
