@@ -182,12 +182,14 @@ typedef struct {
                                    every launch covers all rows (0 = as many as keep one
                                    launch's postings within ~48 MB, so that they stay in
                                    L2 while every row reads them; at most 16)              */
-    int32_t no_fixed_point;     /* float32 only.  0 (default): from the second S-block
-                                   launch on, a row whose current k-th score is large
-                                   enough sums its scan in fixed point (power-of-two scale
-                                   under |r| max|s|; the absolute error stays below 2^-18
-                                   of that k-th score, 4e-6 relative); 1: every scan sums
-                                   in fp32                                                 */
+    int32_t no_fixed_point;     /* float32 with one S-block group per row.  0 (default):
+                                   each row sums its scan in int32 fixed point (scale: the
+                                   largest power of two keeping |r| max|s| below 2^30); a
+                                   row where one fixed-point unit exceeds 2^-23 of the
+                                   smallest score it returns is joined again in fp32 by one
+                                   more launch, so every returned score carries no larger
+                                   an error bound than an fp32 sum (n 2^-24 relative for n
+                                   terms).  1: every scan sums in fp32.                    */
 } knn_join_opts;
 
 /* Top-k of the union of several S shards (no paper counterpart: the exchange step of
@@ -217,8 +219,8 @@ knn_status knn_merge_topk(int32_t n_parts, const int32_t* const* part_ids, const
 #define KNN_STAT_SHARED_ADDS 8      /* shared-memory adds issued by the scan: every posting
                                        slot of the 16-byte chunks read, the zero-weight
                                        padding and the slots past a level's prefix included */
-#define KNN_STAT_FIXED_POINT_ROWS 9 /* (row, S-block launch) pairs whose scan summed in fixed
-                                       point (float joins; see no_fixed_point)              */
+#define KNN_STAT_FIXED_POINT_ROWS 9 /* (row, S-block launch or group) pairs whose scan
+                                       summed in fixed point (float joins; no_fixed_point)   */
 #define KNN_STATS_LEN 10
 
 /* Exact top-k of every row of R against the indexed S.
@@ -281,7 +283,9 @@ typedef struct {
  * blocks into groups of blocks_per_group, orders the work items (largest first) and,
  * with use_graph, captures the launch sequence into a CUDA graph.  The jobs' arrays
  * must stay valid and unchanged in size while the batch exists (contents may change
- * between launches).                                                                 */
+ * between launches).  Float batches run two persistent passes per launch: every row in
+ * fixed point (as knn_join_opts.no_fixed_point = 0 describes), then the rows it flagged
+ * in fp32.                                                                           */
 knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, const knn_batch_opts* opts,
                             void* stream, knn_batch** out);
 /* Runs every job (asynchronously on `stream`): one persistent kernel takes the work
@@ -414,6 +418,9 @@ knn_status knn_threshold_model_params(const knn_model* model, const float** para
  *     S-block launches) is the library's fixed array;
  *   - R must be in device memory, outputs are device memory (outputs_on_host = 0);
  *   - rows are always scanned with one S-block group per row (s_groups is ignored);
+ *   - float scans always sum in fp32 (no_fixed_point is taken as 1: the fixed-point path
+ *     needs a per-row flag array), so float scores may differ from knn_join's in the
+ *     last bits;
  *   - n_rows * k must not exceed (KNN_NOALLOC_SCRATCH_BYTES - 256) / 8 = 2,097,120,
  *     else KNN_EUNSUPPORTED with a message naming the limit.
  * Set-up: the first call on a device (with that device current) looks up the array's

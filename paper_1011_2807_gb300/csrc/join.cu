@@ -215,8 +215,9 @@ struct JoinParams {
     const uint32_t* ubound;
     int64_t u_stride;   // elements between levels of n_unidx / ubound (|S|, or a staged slice's)
     float s_maxnorm;    // largest L2 norm of an S vector, rounded up (float scores: fixed-point scale)
-    uint8_t* fx_done;   // float, S-block-synchronous: per row, 1 if the fixed-point launch of this
-                        // S range joined it (the fp32 launch then skips it), else 0
+    uint8_t* fx_flag;   // float joins in fixed point: per row, set to 1 by the fixed-point launches
+                        // when the row must be joined again in fp32; the fp32 re-join launch
+                        // joins only the rows set
     float levels[KNN_MAX_LEVELS];
     int32_t k, groups, blocks_per_group, iiib, max_r_nnz;
     int32_t bf;         // brute force: every s scored in full (Algorithm 2), no posting scan
@@ -439,32 +440,31 @@ __device__ __forceinline__ void prepare_block_warp(const JoinParams& p, const in
     if (lane == 0) ipre[rn] = carry;
 }
 
-// Float rows may accumulate the scan in fixed point: each product r[d] w times a
-// power-of-two scale, rounded to an integer, added with an integer shared-memory
-// atomic (2.5x the rate of the float one on this GPU), and integer sums do not depend
-// on the order of the adds.  The scale keeps every partial below 2^30 -- a score, and any
-// one product, is at most |r| max|s| (Cauchy-Schwarz) -- so a partial converted back is
-// off by at most n / (2 scale) (n = nnz(r) rounded terms) besides fp32's relative
-// rounding of the products and of the conversion.  A row takes this path only when
-// that absolute error is at most 2^-18 of its current k-th score, which only grows, so
-// every score it returns keeps the error below 4e-6 relative; that needs the k-th
-// score carried in from earlier S blocks.  Nothing else changes: the kernel ranks the
-// converted partials like fp32 ones, and every bound of the cut is stated in terms of
-// the computed partial.
+// Float joins sum the scan in fixed point: each product r[d] w times a power-of-two
+// scale, rounded to an integer, added with an integer shared-memory atomic (2.5x the
+// rate of the float one on this GPU), and integer sums do not depend on the order of
+// the adds.  The scale keeps every partial below 2^30 -- a score, and any one product,
+// is at most |r| max|s| (Cauchy-Schwarz) -- so a partial converted back is off by at
+// most n / (2 scale) (n = nnz(r) rounded terms) besides fp32's relative rounding of the
+// products and of the conversion.  Nothing else changes: the kernel ranks the converted
+// partials like fp32 ones, and every bound of the cut is stated in terms of the
+// computed partial.  When a row is done, one unit (1 / scale) must be at most 2^-23 of
+// the smallest score it returns: each rounded term then errs by no more than an fp32
+// rounding at that magnitude (2^-24 of it), so the fixed-point sum's error bound is no
+// larger than that of the fp32 sum it replaces (n 2^-24 relative for n terms).  A row
+// that fails, or that has no usable scale, is flagged and joined again in fp32.
 template <class S>
-__device__ void fx_decide(const JoinParams& p, S& st, int rn) {
+__device__ void fx_decide(const JoinParams& p, S& st) {
     st.fx = 0;
     st.fx_scale = 1.0f;
     st.fx_inv = 1.0f;
-    if (!st.kth || !(p.s_maxnorm >= 1e-18f) || !(st.fx_rsq > 0.0) || !(st.fx_rsq < 1e300)) return;
-    const double th = (double)__uint_as_float((uint32_t)(st.kth >> 32));
+    if (!(p.s_maxnorm >= 1e-18f) || !(st.fx_rsq > 0.0) || !(st.fx_rsq < 1e300)) return;
     const double ub = sqrt(st.fx_rsq) * (1.0 + 1e-9) * (double)p.s_maxnorm;
     int e;
     frexp(ub, &e);                   // ub < 2^e
     const int es = 30 - e;           // scale 2^es: ub * scale < 2^30
     if (es > 100 || es < -100) return;
     const double scale = ldexp(1.0, es);
-    if (0.5 * (double)rn / scale > th * (1.0 / 262144.0)) return;
     st.fx = 1;
     st.fx_scale = (float)scale;
     st.fx_inv = (float)(1.0 / scale);
@@ -476,12 +476,12 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                                          unsigned char* smem) {
     using Acc = typename JT<W>::Acc;
     using Post = typename JT<W>::Post;
-    // FX: the fixed-point launch of a float join (rows whose precision test fails are left
-    // to the fp32 launch that follows); otherwise the fp32 (or integer) join, which skips
-    // rows the fixed-point launch already joined
+    // FX: a fixed-point launch of a float join (fx_decide); otherwise the fp32 (or
+    // integer) join, which, when given the fixed-point launches' flags, joins only the
+    // rows they flagged
     constexpr bool FXABLE = JT<W>::FIXED_OK && !BF && FX;
     if constexpr (JT<W>::FIXED_OK && !BF && !FX) {
-        if (p.fx_done && p.fx_done[row]) return;
+        if (p.fx_flag && !p.fx_flag[row]) return;
     }
     __shared__ CtaState st;
     __shared__ uint32_t red_m[32];
@@ -571,11 +571,11 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
         }
     }
     if (FXABLE && tid == 0) {
-        fx_decide(p, st, rn);
-        p.fx_done[row] = (uint8_t)st.fx;
+        fx_decide(p, st);
+        if (!st.fx) p.fx_flag[row] = 1;   // no usable scale: the fp32 re-join takes the row
     }
     __syncthreads();
-    if (FXABLE && !st.fx) return;   // the fp32 launch joins this row over the same S blocks
+    if (FXABLE && !st.fx) return;
 
     uint32_t n_cand = 0, n_comp = 0, n_push = 0, n_resf = 0;   // this thread's counters
     unsigned long long n_post = 0, n_add = 0;   // postings scanned; shared-memory adds issued
@@ -1039,6 +1039,10 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
             ((uint32_t*)p.out_scores)[o] = key ? (uint32_t)(key >> 32) : 0u;
         }
         if (tid == 0 && p.n_found) p.n_found[row] = st.size;
+        if (FXABLE && tid == 0 && st.size > 0) {   // one fixed-point unit against the smallest score returned
+            const double th = (double)__uint_as_float((uint32_t)(topk[st.size - 1] >> 32));
+            if ((double)st.fx_scale * th < 8388608.0) p.fx_flag[row] = 1;
+        }
     } else {
         for (int q = tid; q < p.k; q += T)
             p.part_keys[((int64_t)row * p.groups + g) * p.k + q] = q < st.size ? topk[q] : 0ull;
@@ -1105,7 +1109,7 @@ static_assert(sizeof(BatchParams) < 32000, "batch parameters must fit the kernel
 // runs out; items of one job and group run side by side, so that group's postings stay
 // in L2 while its rows read them, and each row's top-k is carried from group to group.
 constexpr long long BATCH_WAIT_SPINS = 1LL << 24;   // default bound: x ~128 ns sleeps, a few seconds
-template <class W, bool COUNT>
+template <class W, bool COUNT, bool FX>
 __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ BatchParams bp,
                                                        unsigned long long* __restrict__ head,
                                                        unsigned* __restrict__ err, long long wait_spins,
@@ -1130,6 +1134,10 @@ __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ B
         const int64_t local = it - bp.item_begin[lo];
         const int g = (int)(local / J.n_rows);
         const int64_t row = local - (int64_t)g * J.n_rows;
+        // the fp32 pass after a fixed-point one joins only the rows that pass flagged: the
+        // other rows' items are skipped before any wait (none of them publishes, and none
+        // of them waits)
+        if (!FX && J.fx_flag && !J.fx_flag[row]) continue;
         // group g continues from group g-1's top-k of this row: that item was taken
         // earlier (items are handed out in order), so it is running or done; wait for
         // it with a bounded spin, and give up with an error flag rather than hang
@@ -1152,8 +1160,12 @@ __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ B
         __syncthreads();
         if (g > 0 && !s_ok) continue;
         const bool last = g == J.groups - 1;
-        join_row<W, COUNT, false, false>(J, row, g, g * J.blocks_per_group, min(J.n_blocks, (g + 1) * J.blocks_per_group),
-                           g > 0, last ? OUT_FINAL : OUT_CARRY, smem);
+        // a row the fixed-point pass flagged early (no usable scale) only passes its groups on
+        const bool skip = FX && g > 0 && *(volatile uint8_t*)(J.fx_flag + row);
+        if (!skip)
+            join_row<W, COUNT, false, FX>(J, row, g, g * J.blocks_per_group,
+                                          min(J.n_blocks, (g + 1) * J.blocks_per_group), g > 0,
+                                          last ? OUT_FINAL : OUT_CARRY, smem);
         if (!last && !no_publish) {   // publish: the carried keys are in global memory before the flag
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -1165,9 +1177,10 @@ __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ B
 }
 
 using BatchKernel = void (*)(const BatchParams, unsigned long long*, unsigned*, long long, int);
-static BatchKernel batch_kernel(knn_dtype dt, bool count) {
-    if (dt == KNN_U8) return count ? k_join_batched<uint8_t, true> : k_join_batched<uint8_t, false>;
-    return count ? k_join_batched<float, true> : k_join_batched<float, false>;
+static BatchKernel batch_kernel(knn_dtype dt, bool count, bool fx = false) {
+    if (dt == KNN_U8) return count ? k_join_batched<uint8_t, true, false> : k_join_batched<uint8_t, false, false>;
+    if (fx) return count ? k_join_batched<float, true, true> : k_join_batched<float, false, true>;
+    return count ? k_join_batched<float, true, false> : k_join_batched<float, false, false>;
 }
 
 // one CTA per row: top-k of the groups' lists
@@ -1492,18 +1505,18 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
         KNN_TRY(stage_setup(ix, per_launch, n_launch, tmp, staged));
         KNN_TRY(stage_copy(ix, 0, per_launch, false, staged));
     }
-    // Float joins over several S-block launches: from the second launch on, the rows whose
-    // carried k-th score proves the fixed-point scan precise enough (fx_decide) are joined
-    // by the fixed-point instance, and the fp32 instance then joins the rest of the rows
-    // over the same S blocks (it skips those marked done).
-    const bool use_fx = ix->dtype == KNN_F32 && !p.bf && groups == 1 && n_launch > 1 && p.s_maxnorm > 0.0f &&
+    // Float joins with one group per row sum their scans in fixed point (fx_decide): every
+    // S-block launch runs the fixed-point instance, and one fp32 launch over all S blocks
+    // then joins again the rows it flagged (no usable scale, or a result whose fixed-point
+    // error is not small enough against its scores); the other rows exit at once.
+    const bool use_fx = ix->dtype == KNN_F32 && !p.bf && groups == 1 && !streamed && p.s_maxnorm > 0.0f &&
                         !o.no_fixed_point;
-    JoinKernel kern_fx = nullptr;
-    uint8_t* fx_done = nullptr;
+    JoinKernel kern_run = kern;
     if (use_fx) {
-        kern_fx = join_kernel(ix->dtype, p.touched || p.stats, false, true);
-        KNN_CUDA_TRY(cudaFuncSetAttribute(kern_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-        KNN_TRY(tmp.get(&fx_done, (size_t)r.n_rows));
+        kern_run = join_kernel(ix->dtype, p.touched || p.stats, false, true);
+        KNN_CUDA_TRY(cudaFuncSetAttribute(kern_run, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+        KNN_TRY(tmp.get(&p.fx_flag, (size_t)r.n_rows));
+        KNN_CUDA_TRY(cudaMemsetAsync(p.fx_flag, 0, (size_t)r.n_rows, stream));
     }
     for (int li = 0; li < n_launch; li++) {
         p.block_begin = li * per_launch;
@@ -1516,16 +1529,19 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
             KNN_CUDA_TRY(cudaStreamWaitEvent(stream, staged.copied[li & 1], 0));
             stage_params(ix, li, per_launch, staged, p);
         }
-        p.fx_done = use_fx && li > 0 ? fx_done : nullptr;
-        if (p.fx_done) {
-            kern_fx<<<(unsigned)grid, T, L.total, stream>>>(p);
-            KNN_CUDA_TRY(cudaGetLastError());
-            count_launch();
-        }
-        kern<<<(unsigned)grid, T, L.total, stream>>>(p);
+        kern_run<<<(unsigned)grid, T, L.total, stream>>>(p);
         KNN_CUDA_TRY(cudaGetLastError());
         count_launch();
         if (streamed) KNN_CUDA_TRY(cudaEventRecord(staged.used[li & 1], stream));
+    }
+    if (use_fx) {   // the fp32 re-join of the flagged rows, over all S blocks in one launch
+        p.block_begin = 0;
+        p.block_end = ix->n_blocks;
+        p.carry_in = 0;
+        p.carry_out = 0;
+        kern<<<(unsigned)grid, T, L.total, stream>>>(p);
+        KNN_CUDA_TRY(cudaGetLastError());
+        count_launch();
     }
     if (groups > 1) {
         int P = 2;
@@ -1753,6 +1769,9 @@ struct knn_batch {
     long long wait_spins = 0;
     int no_publish = 0;
     bool count = false;            // stats requested: the posting-counting kernel instance
+    bool fx = false;               // float: a fixed-point pass, then an fp32 pass of the flagged rows
+    uint8_t* fx_flag = nullptr;    // per row of every job: flagged by the fixed-point pass
+    size_t fx_n = 0;
     int64_t n_items_all = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1762,15 +1781,20 @@ struct knn_batch {
 namespace knn {
 
 static knn_status batch_enqueue(const knn_batch* b, cudaStream_t s) {
-    KNN_CUDA_TRY(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned long long) * b->chunks.size(), s));
     KNN_CUDA_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), s));
-    if (b->done_n) KNN_CUDA_TRY(cudaMemsetAsync(b->done, 0, sizeof(int32_t) * b->done_n, s));
-    for (size_t c = 0; c < b->chunks.size(); c++) {
-        const BatchParams& bp = b->chunks[c];
-        if (bp.item_begin[bp.n_jobs] == 0) continue;
-        batch_kernel(b->dtype, b->count)<<<b->grid, b->T, b->smem, s>>>(bp, b->d_head + c, b->d_err, b->wait_spins,
-                                                                         b->no_publish);
-        KNN_CUDA_TRY(cudaGetLastError());
+    if (b->fx) KNN_CUDA_TRY(cudaMemsetAsync(b->fx_flag, 0, b->fx_n, s));
+    // float batches: the fixed-point pass over every item, then the fp32 pass that joins
+    // the rows it flagged; otherwise the one pass
+    for (int pass = b->fx ? 0 : 1; pass < 2; pass++) {
+        KNN_CUDA_TRY(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned long long) * b->chunks.size(), s));
+        if (b->done_n) KNN_CUDA_TRY(cudaMemsetAsync(b->done, 0, sizeof(int32_t) * b->done_n, s));
+        const BatchKernel kern = batch_kernel(b->dtype, b->count, pass == 0);
+        for (size_t c = 0; c < b->chunks.size(); c++) {
+            const BatchParams& bp = b->chunks[c];
+            if (bp.item_begin[bp.n_jobs] == 0) continue;
+            kern<<<b->grid, b->T, b->smem, s>>>(bp, b->d_head + c, b->d_err, b->wait_spins, b->no_publish);
+            KNN_CUDA_TRY(cudaGetLastError());
+        }
     }
     return KNN_OK;
 }
@@ -1907,6 +1931,18 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
             b->done_n += (size_t)p.n_rows;
         }
     }
+    // float batches: per row of every job, the fixed-point pass's flag (join again in fp32)
+    b->fx = b->dtype == KNN_F32;
+    if (b->fx) {
+        for (int j = 0; j < n_jobs; j++) b->fx_n += (size_t)std::max<int64_t>(0, hj[j].p.n_rows);
+        knn_status st = b->bufs->get(&b->fx_flag, std::max<size_t>(1, b->fx_n));
+        if (st != KNN_OK) return bail(st);
+        size_t off = 0;
+        for (int j = 0; j < n_jobs; j++) {
+            hj[j].p.fx_flag = b->fx_flag + off;
+            off += (size_t)std::max<int64_t>(0, hj[j].p.n_rows);
+        }
+    }
     if (b->done_n) {
         knn_status st = b->bufs->get(&b->done, b->done_n);
         if (st != KNN_OK) return bail(st);
@@ -1946,12 +1982,16 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
     } while (0)
     int per_sm = 0;
     b->count = o.stats != nullptr;
-    const BatchKernel kern = batch_kernel(b->dtype, b->count);
-    BATCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-    BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, b->smem));
+    for (int pass = b->fx ? 0 : 1; pass < 2; pass++) {
+        const BatchKernel kern = batch_kernel(b->dtype, b->count, pass == 0);
+        int ps = 0;
+        BATCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+        BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kern, T, b->smem));
+        per_sm = per_sm ? std::min(per_sm, ps) : ps;
+    }
     if (per_sm < 1) return bail(fail(KNN_EUNSUPPORTED, "the batched kernel does not fit an SM"));
     b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, std::max<int64_t>(1, b->total)));
-    b->launches_per_run = (int)b->chunks.size();
+    b->launches_per_run = (int)b->chunks.size() * (b->fx ? 2 : 1);
     BATCH_CUDA(cudaStreamSynchronize(stream));
     tmp.release();
     if (o.use_graph) {

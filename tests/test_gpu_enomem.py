@@ -44,8 +44,8 @@ class FailingAllocator:
             self.outstanding[int(p)] = int(nbytes)
             return p
 
-        def free(ptr, nbytes, stream, ctx):
-            self.outstanding.pop(int(ptr))
+        def free(ptr, nbytes, stream, ctx):   # buffers from before the install come back here too
+            self.outstanding.pop(int(ptr), None)
             torch.cuda.caching_allocator_delete(int(ptr))
 
         self.cbs = (B._ALLOC_FN(alloc), B._FREE_FN(free))
