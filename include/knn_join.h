@@ -174,8 +174,9 @@ typedef struct {
                                    synchronises `stream` before returning                */
     int32_t skip_validation;    /* 1: trust R (sorted, in range, w > 0)                   */
     float level_margin;         /* Section 4.4 cut per S block: the highest level l with
-                                   M * L_l <= level_margin * theta (0 = 0.3).  Lower values
-                                   scan more postings and complete fewer candidates.     */
+                                   M * L_l <= level_margin * theta (0 = 0.3 for a uint8
+                                   index, 0.2 for float32).  Lower values scan more
+                                   postings and complete fewer candidates.               */
     int64_t* stats;             /* device int64[KNN_STATS_LEN] or NULL: work counters,
                                    added to (see KNN_STAT_*)                              */
     int32_t blocks_per_launch;  /* with one group per row: S blocks per kernel launch;
@@ -231,7 +232,10 @@ knn_status knn_merge_topk(int32_t n_parts, const int32_t* const* part_ids, const
  *   out_scores  int32 (KNN_U8) or float (KNN_F32) [n_rows * k], 0 padding.
  * Row i lists min(k, #{s : dot(r_i, s) > 0}) entries (with init_threshold: those with
  * dot >= init_threshold[i]) ordered by (score desc, id asc).
- * Synchronises `stream` (it reads R's size and longest row back to size the launch).
+ * Synchronises `stream` (it reads R's size and longest row back to size the launch;
+ * when R's longest rows need a shared-memory layout above 110 KB, i.e. one CTA per SM,
+ * it also reads back how many rows fit a smaller one: those rows then run in launches
+ * of their own at two CTAs per SM, the long rows in launches with the full layout).
  * Errors: KNN_EINVAL (bad R, dim/dtype mismatch, k < 1), KNN_EUNSUPPORTED (k > 64,
  * a row too long for one CTA's shared memory, u8 scores that could overflow int32),
  * KNN_ENOMEM, KNN_ECUDA.                                                           */
@@ -258,7 +262,7 @@ typedef struct {
                                    Every job's S block must lie in [4*threads, 64*threads]. */
     int32_t blocks_per_group;   /* S blocks per work item; 0 = as blocks_per_launch's default,
                                    per job (~48 MB of postings, at most 16)                */
-    float level_margin;         /* as in knn_join_opts (0 = 0.3)                             */
+    float level_margin;         /* as in knn_join_opts (0 = 0.3, 0.2 for a float32 index)  */
     int32_t use_graph;          /* knn_batch_create: capture the launch into a CUDA graph   */
     int32_t skip_validation;    /* 1: trust every R                                          */
     int64_t* stats;             /* device int64[KNN_STATS_LEN] or NULL (all jobs together)   */

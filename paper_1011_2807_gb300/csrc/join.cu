@@ -215,6 +215,7 @@ struct JoinParams {
     const uint32_t* ubound;
     int64_t u_stride;   // elements between levels of n_unidx / ubound (|S|, or a staged slice's)
     float s_maxnorm;    // largest L2 norm of an S vector, rounded up (float scores: fixed-point scale)
+    const int32_t* row_list;   // one group per row: the rows of this launch (NULL: row = CTA index)
     uint8_t* fx_flag;   // float joins in fixed point: per row, set to 1 by the fixed-point launches
                         // when the row must be joined again in fp32; the fp32 re-join launch
                         // joins only the rows set
@@ -1068,8 +1069,8 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
 template <class W, bool COUNT, bool BF, bool FX>
 __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int64_t row = blockIdx.x / p.groups;
-    const int g = blockIdx.x - (int)(row * p.groups);
+    const int64_t row = p.row_list ? (int64_t)p.row_list[blockIdx.x] : (int64_t)(blockIdx.x / p.groups);
+    const int g = p.row_list ? 0 : (int)(blockIdx.x - row * p.groups);
     if (p.groups == 1)
         join_row<W, COUNT, BF, FX>(p, row, 0, p.block_begin, p.block_end, p.carry_in != 0,
                                    p.carry_out ? OUT_CARRY : OUT_FINAL, smem);
@@ -1183,6 +1184,16 @@ static BatchKernel batch_kernel(knn_dtype dt, bool count, bool fx = false) {
     return count ? k_join_batched<float, true, false> : k_join_batched<float, false, false>;
 }
 
+// Rows with at most r_short features to the front of `lists`, the others to the back
+// (each part in no particular order); counts[0] / counts[1] count them.
+__global__ void k_split_rows(const int64_t* __restrict__ indptr, int64_t n, int32_t r_short,
+                             int32_t* __restrict__ lists, int32_t* __restrict__ counts) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (indptr[i + 1] - indptr[i] <= r_short) lists[atomicAdd(&counts[0], 1)] = (int32_t)i;
+    else lists[n - 1 - atomicAdd(&counts[1], 1)] = (int32_t)i;
+}
+
 // one CTA per row: top-k of the groups' lists
 __global__ void k_merge_groups(const u64* __restrict__ part, int64_t n_rows, int groups, int k, int P,
                                int32_t* out_ids, uint32_t* out_scores, int32_t* n_found) {
@@ -1279,6 +1290,11 @@ static int default_blocks_per_launch(const knn_index* ix) {
     const int b = per_block > 0.0 ? (int)std::min(16.0, 48.0e6 / per_block) : 16;
     return std::max(1, b);
 }
+
+// Level margin when the caller gives none (section 4.2's trade of postings scanned against
+// completions): 0.3 for uint8 scores; 0.2 for float scores, whose completions look r's
+// weights up by binary search (measured best on the float workload at |S| = 10M).
+static float default_margin(knn_dtype dt) { return dt == KNN_F32 ? 0.2f : 0.3f; }
 
 // the largest L2 norm of an S vector as a float not below it (0 when unknown or not finite)
 static float maxnorm_up(const knn_index* ix) {
@@ -1482,7 +1498,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     p.n_found = o.n_found;
     p.touched = (unsigned long long*)o.postings_scanned;
     p.stats = (unsigned long long*)o.stats;
-    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 0.3f;
+    p.level_margin = o.level_margin > 0.0f ? o.level_margin : default_margin(ix->dtype);
     if (!(p.level_margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     if (groups > 1) {
         KNN_TRY(tmp.get(&p.part_keys, (size_t)r.n_rows * groups * k));
@@ -1518,6 +1534,67 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
         KNN_TRY(tmp.get(&p.fx_flag, (size_t)r.n_rows));
         KNN_CUDA_TRY(cudaMemsetAsync(p.fx_flag, 0, (size_t)r.n_rows, stream));
     }
+    // With one group per row, when the longest rows need a shared-memory layout that
+    // leaves room for one CTA per SM only, every launch runs in two parts: the rows with at
+    // most r_short features (the most a layout within 110 KB -- two CTAs per SM -- holds)
+    // with that layout, then the longer rows with the full one.  Rows are independent, so
+    // splitting them changes nothing but occupancy.
+    int r_short = 0, rden_short = 0, n_short = 0;
+    int32_t* row_lists = nullptr;
+    size_t smem_short = 0;
+    if (groups == 1 && r.n_rows > 1 && L.total > 110 * 1024) {
+        auto rden_for = [&](int q) {
+            if (ix->dtype != KNN_U8 || ix->dim > 32768) return 0;
+            const int rd = (int)((ix->dim + 15) & ~15);
+            return smem_layout(nb, q, rd).total <= 110 * 1024 ? rd : 0;
+        };
+        for (int q = max_r - 1; q >= 32; q--)
+            if (smem_layout(nb, q, rden_for(q)).total <= 110 * 1024) {
+                r_short = q;
+                break;
+            }
+        if (r_short > 0) {
+            rden_short = rden_for(r_short);
+            smem_short = smem_layout(nb, r_short, rden_short).total;
+            int32_t* counts = nullptr;
+            KNN_TRY(tmp.get(&row_lists, (size_t)r.n_rows));
+            KNN_TRY(tmp.get(&counts, 2));
+            KNN_CUDA_TRY(cudaMemsetAsync(counts, 0, 2 * sizeof(int32_t), stream));
+            k_split_rows<<<launch_blocks(r.n_rows, 256), 256, 0, stream>>>(r.indptr, r.n_rows, r_short, row_lists,
+                                                                          counts);
+            KNN_CUDA_TRY(cudaGetLastError());
+            count_launch();
+            int32_t hc[2] = {0, 0};
+            KNN_CUDA_TRY(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, stream));
+            KNN_CUDA_TRY(cudaStreamSynchronize(stream));
+            n_short = hc[0];
+        }
+    }
+    auto launch_rows = [&](JoinKernel kf, const JoinParams& q) -> knn_status {
+        if (!r_short) {
+            kf<<<(unsigned)grid, T, L.total, stream>>>(q);
+            KNN_CUDA_TRY(cudaGetLastError());
+            count_launch();
+            return KNN_OK;
+        }
+        if (n_short > 0) {
+            JoinParams qs = q;
+            qs.row_list = row_lists;
+            qs.max_r_nnz = r_short;
+            qs.rden_dim = rden_short;
+            kf<<<(unsigned)n_short, T, smem_short, stream>>>(qs);
+            KNN_CUDA_TRY(cudaGetLastError());
+            count_launch();
+        }
+        if (n_short < r.n_rows) {
+            JoinParams ql = q;
+            ql.row_list = row_lists + n_short;
+            kf<<<(unsigned)(r.n_rows - n_short), T, L.total, stream>>>(ql);
+            KNN_CUDA_TRY(cudaGetLastError());
+            count_launch();
+        }
+        return KNN_OK;
+    };
     for (int li = 0; li < n_launch; li++) {
         p.block_begin = li * per_launch;
         p.block_end = std::min(ix->n_blocks, (li + 1) * per_launch);
@@ -1529,9 +1606,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
             KNN_CUDA_TRY(cudaStreamWaitEvent(stream, staged.copied[li & 1], 0));
             stage_params(ix, li, per_launch, staged, p);
         }
-        kern_run<<<(unsigned)grid, T, L.total, stream>>>(p);
-        KNN_CUDA_TRY(cudaGetLastError());
-        count_launch();
+        KNN_TRY(launch_rows(kern_run, p));
         if (streamed) KNN_CUDA_TRY(cudaEventRecord(staged.used[li & 1], stream));
     }
     if (use_fx) {   // the fp32 re-join of the flagged rows, over all S blocks in one launch
@@ -1539,9 +1614,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
         p.block_end = ix->n_blocks;
         p.carry_in = 0;
         p.carry_out = 0;
-        kern<<<(unsigned)grid, T, L.total, stream>>>(p);
-        KNN_CUDA_TRY(cudaGetLastError());
-        count_launch();
+        KNN_TRY(launch_rows(kern, p));
     }
     if (groups > 1) {
         int P = 2;
@@ -1728,7 +1801,7 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     p.n_found = o.n_found;
     p.touched = (unsigned long long*)o.postings_scanned;
     p.stats = (unsigned long long*)o.stats;
-    p.level_margin = o.level_margin > 0.0f ? o.level_margin : 0.3f;
+    p.level_margin = o.level_margin > 0.0f ? o.level_margin : default_margin(ix->dtype);
     if (!(p.level_margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     p.carry = (u64*)((unsigned char*)scratch + NOALLOC_HEADER);
 
@@ -1822,7 +1895,9 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
     knn_batch_opts o = {};
     if (opts) o = *opts;
     if (o.mode != KNN_MODE_IIIB && o.mode != KNN_MODE_IIB) return fail(KNN_EINVAL, "unknown mode");
-    const float margin = o.level_margin > 0.0f ? o.level_margin : 0.3f;
+    const float margin = o.level_margin > 0.0f
+                             ? o.level_margin
+                             : default_margin(jobs[0].index ? jobs[0].index->dtype : KNN_U8);
     if (!(margin <= 1.0f)) return fail(KNN_EINVAL, "level_margin must be in (0, 1]");
     int dev = 0, smem_optin = 0, n_sm = 0;
     KNN_CUDA_TRY(cudaGetDevice(&dev));

@@ -121,6 +121,50 @@ def test_largest_s_block(knn, oracle_mod, mode):
     compare.assert_exact(ids, sc, eids, esc, f"block 32768 {mode}")
 
 
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_long_rows_run_in_a_launch_of_their_own(knn, oracle_mod, dtype):
+    """A few query rows too long for a two-CTA-per-SM shared-memory layout among short
+    ones: each S-block launch runs the short rows with the small layout and the long rows
+    with the full one.  Results against the oracle (uint8 bit-exact), for S-block-
+    synchronous launches, the fp32 re-join path and one launch over all S blocks."""
+    import torch
+    from paper_1011_2807_gb300.binding import KNN_STATS
+    rng = np.random.default_rng(961)
+    dim = 6000
+    if dtype == "u8":
+        S = random_u8(9000, dim, 80, 962, nnz_lo=10)
+        short = [list(zip(np.sort(rng.choice(dim, int(rng.integers(5, 200)), replace=False)).tolist(),
+                          rng.integers(1, 101, 1000).tolist())) for _ in range(60)]
+        long_ = [list(zip(np.sort(rng.choice(dim, n, replace=False)).tolist(), rng.integers(1, 101, n).tolist()))
+                 for n in (900, 1400, 2500)]
+        rows = short[:30] + long_ + short[30:]
+        R = synth.from_rows([[(d, w) for d, w in r] for r in rows], dim, np.uint8)
+    else:
+        S = synth.zipf_f32(9000, 963, dim=dim, nnz_hi=300)
+        short = [list(zip(np.sort(rng.choice(dim, int(rng.integers(5, 200)), replace=False)).tolist(),
+                          rng.lognormal(0.0, 1.0, 1000).tolist())) for _ in range(60)]
+        long_ = [list(zip(np.sort(rng.choice(dim, n, replace=False)).tolist(), rng.lognormal(0.0, 1.0, n).tolist()))
+                 for n in (1200, 1800, 2500)]
+        rows = short[:30] + long_ + short[30:]
+        R = synth.from_rows(rows, dim, np.float32)
+    k = 9
+    eids, esc, _ = oracle_mod.bf_join(R, S, k, threads=8)
+    idx = knn.knn_join_build_index(S, block_size=1024)
+    Rd = knn.DeviceCSR.from_host(R)
+    for kw in (dict(blocks_per_launch=2), dict(blocks_per_launch=2, mode="iib"), dict(blocks_per_launch=100),
+               dict(blocks_per_launch=3, fixed_point=False)):
+        st = torch.zeros(len(KNN_STATS), dtype=torch.int64, device="cuda")
+        ids, sc = knn.knn_join(idx, Rd, k, s_groups=1, stats=st, **kw)
+        ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+        if dtype == "u8":
+            compare.assert_exact(ids, sc, eids, esc, f"long rows {kw}")
+        else:
+            compare.assert_close(R, S, list(range(R.n_rows)), ids, sc, eids, esc, what=f"long rows {kw}")
+        w = dict(zip(KNN_STATS, st.cpu().tolist()))
+        assert w["block_steps"] >= R.n_rows * idx.info()["n_blocks"]   # every row, every block
+    idx.close()
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_random_small_dims_many_ties(knn, oracle_mod, seed):
     # few dimensions and weights in {1,2}: scores tie everywhere
