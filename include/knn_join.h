@@ -277,8 +277,8 @@ typedef struct knn_batch knn_batch;   /* a prepared batch (validated jobs, work 
 
 typedef struct {
     int64_t work_items;       /* (job, S-block group, row) items of one run              */
-    int32_t ctas, threads;    /* persistent grid                                          */
-    int64_t shared_bytes;     /* dynamic shared memory per CTA                            */
+    int32_t ctas, threads;    /* persistent grid (the largest of its launches)            */
+    int64_t shared_bytes;     /* dynamic shared memory per CTA (the largest)              */
     int32_t graph;            /* 1 if runs replay a captured CUDA graph                  */
     int32_t kernels_per_launch;
 } knn_batch_info;
@@ -286,10 +286,15 @@ typedef struct {
 /* Prepares n_jobs joins: validates each R (synchronises `stream`), splits each job's S
  * blocks into groups of blocks_per_group, orders the work items (largest first) and,
  * with use_graph, captures the launch sequence into a CUDA graph.  The jobs' arrays
- * must stay valid and unchanged in size while the batch exists (contents may change
- * between launches).  Float batches run two persistent passes per launch: every row in
- * fixed point (as knn_join_opts.no_fixed_point = 0 describes), then the rows it flagged
- * in fp32.                                                                           */
+ * must stay valid and unchanged in size while the batch exists; R's column indices and
+ * values may change between launches, its row lengths (indptr) may not: a row longer
+ * than at creation is not joined, and knn_batch_check reports KNN_EINVAL.  A job whose
+ * longest rows need a shared-memory layout above 110 KB (one CTA per SM) is split once
+ * here (one read-back): its rows that fit a layout within 110 KB run in a persistent
+ * launch with the other such jobs at two CTAs per SM, the longer rows in a launch of
+ * their own.  Float batches run two persistent passes per launch: every row in fixed
+ * point (as knn_join_opts.no_fixed_point = 0 describes), then the rows it flagged in
+ * fp32.                                                                              */
 knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, const knn_batch_opts* opts,
                             void* stream, knn_batch** out);
 /* Runs every job (asynchronously on `stream`): one persistent kernel takes the work
@@ -297,8 +302,9 @@ knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, const knn_batch
  * left (a bounded wait if that item is still running).  Results land in each job's
  * outputs exactly as knn_join would write them.                                     */
 knn_status knn_batch_launch(knn_batch* batch, void* stream);
-/* Synchronises `stream` and reports the last run: KNN_ETIMEOUT if a work item gave up
- * its bounded wait for the previous S-block group of its row (its outputs are then
+/* Synchronises `stream` and reports the last run: KNN_EINVAL if a row had more
+ * features than when the batch was made, KNN_ETIMEOUT if a work item gave up its
+ * bounded wait for the previous S-block group of its row (that row's outputs are then
  * incomplete), else KNN_OK.                                                         */
 knn_status knn_batch_check(const knn_batch* batch, void* stream);
 knn_status knn_batch_get_info(const knn_batch* batch, knn_batch_info* info);

@@ -1069,8 +1069,8 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
 template <class W, bool COUNT, bool BF, bool FX>
 __global__ void __launch_bounds__(1024) k_join(JoinParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int64_t row = p.row_list ? (int64_t)p.row_list[blockIdx.x] : (int64_t)(blockIdx.x / p.groups);
-    const int g = p.row_list ? 0 : (int)(blockIdx.x - row * p.groups);
+    const int row = p.row_list ? p.row_list[blockIdx.x] : (int)(blockIdx.x / p.groups);   // rows < 2^31
+    const int g = p.row_list ? 0 : (int)(blockIdx.x - (unsigned)row * p.groups);
     if (p.groups == 1)
         join_row<W, COUNT, BF, FX>(p, row, 0, p.block_begin, p.block_end, p.carry_in != 0,
                                    p.carry_out ? OUT_CARRY : OUT_FINAL, smem);
@@ -1116,50 +1116,73 @@ __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ B
                                                        unsigned* __restrict__ err, long long wait_spins,
                                                        int no_publish) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_item;
-    __shared__ bool s_ok;
+    // the item's job (-1: no items left), S-block group and row, decoded by thread 0
+    __shared__ int s_job, s_g, s_row, s_ok;
     const long long total = bp.item_begin[bp.n_jobs];
     for (;;) {
         __syncthreads();   // the previous item is finished with shared memory
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(head, 1ull);
-        __syncthreads();
-        const long long it = s_item;
-        if (it >= total) break;
-        int lo = 0, hi = bp.n_jobs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (bp.item_begin[mid] <= it) lo = mid;
-            else hi = mid - 1;
-        }
-        const JoinParams& J = bp.p[lo];
-        const int64_t local = it - bp.item_begin[lo];
-        const int g = (int)(local / J.n_rows);
-        const int64_t row = local - (int64_t)g * J.n_rows;
-        // the fp32 pass after a fixed-point one joins only the rows that pass flagged: the
-        // other rows' items are skipped before any wait (none of them publishes, and none
-        // of them waits)
-        if (!FX && J.fx_flag && !J.fx_flag[row]) continue;
-        // group g continues from group g-1's top-k of this row: that item was taken
-        // earlier (items are handed out in order), so it is running or done; wait for
-        // it with a bounded spin, and give up with an error flag rather than hang
-        if (g > 0 && threadIdx.x == 0) {
-            int* dp = J.done + row;
-            long long spins = 0;
-            int v = 0;
-            for (;;) {
-                asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(dp) : "memory");
-                if (v >= g || v < 0) break;   // ready, or an earlier group of this row failed
-                if (++spins > wait_spins) break;
-                __nanosleep(128);
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(head, 1ull);
+            int lo = -1, g = 0, ok = 0;
+            int64_t row = 0;
+            if (it < total) {
+                lo = 0;
+                int hi = bp.n_jobs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (bp.item_begin[mid] <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                const JoinParams& J = bp.p[lo];
+                const int64_t local = it - bp.item_begin[lo];
+                const int64_t n_list = (bp.item_begin[lo + 1] - bp.item_begin[lo]) / J.groups;   // rows it covers
+                g = (int)(local / n_list);
+                const int64_t li = local - (int64_t)g * n_list;
+                row = J.row_list ? (int64_t)J.row_list[li] : li;
+                ok = 1;
+                // the fp32 pass after a fixed-point one joins only the rows that pass
+                // flagged: the other rows' items are skipped before any wait (none of them
+                // publishes, and none of them waits)
+                if (!FX && J.fx_flag && !J.fx_flag[row]) ok = 0;
+                // group g continues from group g-1's top-k of this row: that item was taken
+                // earlier (items are handed out in order), so it is running or done; wait
+                // for it with a bounded spin, and give up with an error flag rather than hang
+                if (ok && g > 0) {
+                    int* dp = J.done + row;
+                    long long spins = 0;
+                    int v = 0;
+                    for (;;) {
+                        asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(dp) : "memory");
+                        if (v >= g || v < 0) break;   // ready, or an earlier group of this row failed
+                        if (++spins > wait_spins) break;
+                        __nanosleep(128);
+                    }
+                    ok = v >= g;
+                    if (!ok) {
+                        if (v >= 0) atomicOr(err, 1u);   // (v < 0: an earlier group's failure, flagged there)
+                        atomicExch(dp, -1);              // later groups of this row give up at once
+                    }
+                }
+                // the shared-memory layout holds rows of up to max_r_nnz features, fixed when
+                // the batch was made: a row that has grown since is not joined (error flag 2)
+                if (ok && J.r_indptr[row + 1] - J.r_indptr[row] > J.max_r_nnz) {
+                    ok = 0;
+                    atomicOr(err, 2u);
+                    if (J.done) atomicExch(J.done + row, -1);
+                }
             }
-            s_ok = v >= g;
-            if (!s_ok) {
-                atomicOr(err, 1u);
-                atomicExch(dp, -1);   // later groups of this row give up at once
-            }
+            s_job = lo;
+            s_g = g;
+            s_row = (int)row;
+            s_ok = ok;
         }
         __syncthreads();
-        if (g > 0 && !s_ok) continue;
+        const int job = s_job;
+        if (job < 0) break;
+        if (!s_ok) continue;
+        const JoinParams& J = bp.p[job];
+        const int g = s_g;
+        const int64_t row = s_row;
         const bool last = g == J.groups - 1;
         // a row the fixed-point pass flagged early (no usable scale) only passes its groups on
         const bool skip = FX && g > 0 && *(volatile uint8_t*)(J.fx_flag + row);
@@ -1170,8 +1193,12 @@ __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ B
         if (!last && !no_publish) {   // publish: the carried keys are in global memory before the flag
             __syncthreads();
             if (threadIdx.x == 0) {
+                // the item, re-read: nothing of it needs to stay in registers across the join
+                const int jb = *(volatile int*)&s_job;
+                const int gg = *(volatile int*)&s_g;
+                const int rr = *(volatile int*)&s_row;
                 __threadfence();
-                asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(J.done + row), "r"(g + 1) : "memory");
+                asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(bp.p[jb].done + rr), "r"(gg + 1) : "memory");
             }
         }
     }
@@ -1182,6 +1209,32 @@ static BatchKernel batch_kernel(knn_dtype dt, bool count, bool fx = false) {
     if (dt == KNN_U8) return count ? k_join_batched<uint8_t, true, false> : k_join_batched<uint8_t, false, false>;
     if (fx) return count ? k_join_batched<float, true, true> : k_join_batched<float, false, true>;
     return count ? k_join_batched<float, true, false> : k_join_batched<float, false, false>;
+}
+
+// A layout within this leaves room for two CTAs of 512 threads per SM.
+constexpr size_t TWO_CTA_SMEM = 110 * 1024;
+
+// Bytes of the dense copy of r's weights (uint8, dimension up to 32768) that a CTA keeps
+// for completions when, with rows of up to max_r features, the layout still leaves room
+// for two CTAs per SM; else 0 (completions then search r's sorted features).
+static int rden_fitting(const knn_index* ix, int nb, int max_r) {
+    if (ix->dtype != KNN_U8 || ix->dim > 32768) return 0;
+    const int rd = (int)((ix->dim + 15) & ~15);
+    return smem_layout(nb, max_r, rd).total <= TWO_CTA_SMEM ? rd : 0;
+}
+
+// The longest row length q < max_r whose layout fits TWO_CTA_SMEM (0 if none from 32 up),
+// with its dense-copy size in *rden.
+static int short_row_limit(const knn_index* ix, int nb, int max_r, int* rden) {
+    for (int q = max_r - 1; q >= 32; q--) {
+        const int rd = rden_fitting(ix, nb, q);
+        if (smem_layout(nb, q, rd).total <= TWO_CTA_SMEM) {
+            *rden = rd;
+            return q;
+        }
+    }
+    *rden = 0;
+    return 0;
 }
 
 // Rows with at most r_short features to the front of `lists`, the others to the back
@@ -1428,11 +1481,7 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     const int max_r = std::max(1, r.max_row_nnz);
     // r's weights kept densely for completions (uint8, dimension up to 32768) when it
     // still leaves room for two CTAs per SM
-    int rden_dim = 0;
-    if (ix->dtype == KNN_U8 && ix->dim <= 32768) {
-        const int rd = (int)((ix->dim + 15) & ~15);
-        if (smem_layout(nb, max_r, rd).total <= 110 * 1024) rden_dim = rd;
-    }
+    const int rden_dim = rden_fitting(ix, nb, max_r);
     SmemLayout L = smem_layout(nb, max_r, rden_dim);
     int dev = 0;
     KNN_CUDA_TRY(cudaGetDevice(&dev));
@@ -1542,19 +1591,9 @@ extern "C" knn_status knn_join(const knn_index* ix, const knn_csr* R, int32_t k,
     int r_short = 0, rden_short = 0, n_short = 0;
     int32_t* row_lists = nullptr;
     size_t smem_short = 0;
-    if (groups == 1 && r.n_rows > 1 && L.total > 110 * 1024) {
-        auto rden_for = [&](int q) {
-            if (ix->dtype != KNN_U8 || ix->dim > 32768) return 0;
-            const int rd = (int)((ix->dim + 15) & ~15);
-            return smem_layout(nb, q, rd).total <= 110 * 1024 ? rd : 0;
-        };
-        for (int q = max_r - 1; q >= 32; q--)
-            if (smem_layout(nb, q, rden_for(q)).total <= 110 * 1024) {
-                r_short = q;
-                break;
-            }
+    if (groups == 1 && r.n_rows > 1 && L.total > TWO_CTA_SMEM) {
+        r_short = short_row_limit(ix, nb, max_r, &rden_short);
         if (r_short > 0) {
-            rden_short = rden_for(r_short);
             smem_short = smem_layout(nb, r_short, rden_short).total;
             int32_t* counts = nullptr;
             KNN_TRY(tmp.get(&row_lists, (size_t)r.n_rows));
@@ -1753,11 +1792,7 @@ extern "C" knn_status knn_join_noalloc(const knn_index* ix, const knn_csr* R, in
     const int max_r = std::max(1, r.max_row_nnz);
     // r's weights kept densely for completions (uint8, dimension up to 32768) when it
     // still leaves room for two CTAs per SM
-    int rden_dim = 0;
-    if (ix->dtype == KNN_U8 && ix->dim <= 32768) {
-        const int rd = (int)((ix->dim + 15) & ~15);
-        if (smem_layout(nb, max_r, rd).total <= 110 * 1024) rden_dim = rd;
-    }
+    const int rden_dim = rden_fitting(ix, nb, max_r);
     SmemLayout L = smem_layout(nb, max_r, rden_dim);
     int dev = 0, smem_optin = 0;
     KNN_CUDA_TRY(cudaGetDevice(&dev));
@@ -1834,7 +1869,9 @@ struct knn_batch {
     int n_jobs = 0, T = 512, grid = 0;
     size_t smem = 0;
     int64_t total = 0;
-    std::vector<knn::BatchParams> chunks;   // up to BATCH_MAX_JOBS jobs per launch
+    std::vector<knn::BatchParams> chunks;   // up to BATCH_MAX_JOBS (sub-)jobs per launch
+    std::vector<size_t> chunk_smem;         // each chunk's layout (its largest)
+    std::vector<int> chunk_grid;            // each chunk's persistent grid
     unsigned long long* d_head = nullptr;   // one work counter per chunk
     unsigned* d_err = nullptr;     // set when a bounded wait gave up
     int32_t* done = nullptr;       // per row of every multi-group job: groups finished
@@ -1865,7 +1902,8 @@ static knn_status batch_enqueue(const knn_batch* b, cudaStream_t s) {
         for (size_t c = 0; c < b->chunks.size(); c++) {
             const BatchParams& bp = b->chunks[c];
             if (bp.item_begin[bp.n_jobs] == 0) continue;
-            kern<<<b->grid, b->T, b->smem, s>>>(bp, b->d_head + c, b->d_err, b->wait_spins, b->no_publish);
+            kern<<<b->chunk_grid[c], b->T, b->chunk_smem[c], s>>>(bp, b->d_head + c, b->d_err, b->wait_spins,
+                                                                 b->no_publish);
             KNN_CUDA_TRY(cudaGetLastError());
         }
     }
@@ -1923,10 +1961,13 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
     struct JobPlan {
         JoinParams p;
         int64_t n_items;
+        size_t smem;         // shared-memory layout for its longest row
+        int r_short = 0;     // > 0: rows up to this length run as a sub-job with a layout within 110 KB
+        int rden_short = 0;
+        int32_t* lists = nullptr;   // its rows, short ones first
     };
     std::vector<JobPlan> hj(n_jobs);
     std::vector<double> cost(n_jobs);
-    size_t smem_max = 0;
     for (int j = 0; j < n_jobs; j++) {
         const knn_job& jb = jobs[j];
         const knn_index* ix = jb.index;
@@ -1948,15 +1989,12 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
             return bail(fail(KNN_EUNSUPPORTED, "job %d: S blocks of %d do not fit %d threads (need 4*T <= block <= 64*T)",
                              j, nb, T));
         const int max_r = std::max(1, r.max_row_nnz);
-        int rden_dim = 0;
-        if (ix->dtype == KNN_U8 && ix->dim <= 32768) {
-            const int rd = (int)((ix->dim + 15) & ~15);
-            if (smem_layout(nb, max_r, rd).total <= 110 * 1024) rden_dim = rd;
-        }
+        const int rden_dim = rden_fitting(ix, nb, max_r);
         const size_t sm = smem_layout(nb, max_r, rden_dim).total;
         if (sm + sizeof(CtaState) + 32 * 8 * 2 + 128 > (size_t)smem_optin)
             return bail(fail(KNN_EUNSUPPORTED, "job %d: needs %zu bytes of shared memory", j, sm));
-        smem_max = std::max(smem_max, sm);
+        hj[j].smem = sm;
+        if (sm > TWO_CTA_SMEM && r.n_rows > 1) hj[j].r_short = short_row_limit(ix, nb, max_r, &hj[j].rden_short);
         int bpg = std::min(o.blocks_per_group > 0 ? o.blocks_per_group : default_blocks_per_launch(ix), ix->n_blocks);
         int groups = (int)ceil_div(ix->n_blocks, bpg);
 
@@ -2028,25 +2066,90 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
                 off += (size_t)hj[j].p.n_rows;
             }
     }
-    std::vector<int> order(n_jobs);
-    for (int j = 0; j < n_jobs; j++) order[j] = j;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-    for (size_t i = 0; i < order.size(); i += BATCH_MAX_JOBS) {
-        BatchParams bp;
-        memset(&bp, 0, sizeof(bp));
-        long long item = 0;
-        for (size_t q = i; q < std::min(order.size(), i + BATCH_MAX_JOBS); q++) {
-            bp.p[bp.n_jobs] = hj[order[q]].p;
-            bp.item_begin[bp.n_jobs] = item;
-            item += hj[order[q]].n_items;
-            bp.n_jobs++;
+    // A job whose longest rows need a layout above TWO_CTA_SMEM (one CTA per SM) is split
+    // in two sub-jobs: its rows of at most r_short features, with the largest layout
+    // within TWO_CTA_SMEM, and the rest with the full one.  Each sub-job lists its rows
+    // (k_split_rows, once here); both share the job's outputs, carried keys, done counters
+    // and flags, which are indexed by the row.
+    int n_split = 0;
+    for (int j = 0; j < n_jobs; j++) n_split += hj[j].r_short > 0;
+    std::vector<int32_t> split_n(2 * (size_t)n_split, 0);
+    if (n_split) {
+        int32_t* counts = nullptr;
+        knn_status st = tmp.get(&counts, 2 * (size_t)n_split);
+        if (st != KNN_OK) return bail(st);
+        if (cudaMemsetAsync(counts, 0, 2 * sizeof(int32_t) * n_split, stream) != cudaSuccess)
+            return bail(fail(KNN_ECUDA, "memset of the row-split counts failed"));
+        for (int j = 0, q = 0; j < n_jobs; j++) {
+            if (!hj[j].r_short) continue;
+            const JoinParams& p = hj[j].p;
+            if ((st = b->bufs->get(&hj[j].lists, (size_t)p.n_rows)) != KNN_OK) return bail(st);
+            k_split_rows<<<launch_blocks(p.n_rows, 256), 256, 0, stream>>>(p.r_indptr, p.n_rows, hj[j].r_short,
+                                                                          hj[j].lists, counts + 2 * q++);
+            if (cudaGetLastError() != cudaSuccess) return bail(fail(KNN_ECUDA, "k_split_rows launch failed"));
+            count_launch();
         }
-        bp.item_begin[bp.n_jobs] = item;
-        b->chunks.push_back(bp);
-        b->n_items_all += item;
+        if (cudaMemcpyAsync(split_n.data(), counts, 2 * sizeof(int32_t) * n_split, cudaMemcpyDeviceToHost, stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess)
+            return bail(fail(KNN_ECUDA, "reading the row-split counts failed"));
+    }
+    struct SubJob {
+        JoinParams p;
+        int64_t n_items;
+        size_t smem;
+        double cost;
+    };
+    std::vector<SubJob> subs;
+    for (int j = 0, q = 0; j < n_jobs; j++) {
+        const JobPlan& h = hj[j];
+        if (!h.r_short) {
+            subs.push_back({h.p, h.n_items, h.smem, cost[j]});
+            continue;
+        }
+        const int64_t n_short = split_n[2 * q++];
+        if (n_short > 0) {
+            SubJob sj{h.p, n_short * h.p.groups, smem_layout(1 << h.p.block_shift, h.r_short, h.rden_short).total,
+                      cost[j]};
+            sj.p.row_list = h.lists;
+            sj.p.max_r_nnz = h.r_short;
+            sj.p.rden_dim = h.rden_short;
+            subs.push_back(sj);
+        }
+        if (n_short < h.p.n_rows) {
+            SubJob sj{h.p, (h.p.n_rows - n_short) * h.p.groups, h.smem, cost[j]};
+            sj.p.row_list = h.lists + n_short;
+            subs.push_back(sj);
+        }
+    }
+    // Chunks: the sub-jobs within TWO_CTA_SMEM, then the others, each class in persistent
+    // launches of up to BATCH_MAX_JOBS sub-jobs, larger items first.
+    for (int cls = 0; cls < 2; cls++) {
+        std::vector<int> order;
+        for (int i = 0; i < (int)subs.size(); i++)
+            if ((subs[i].smem > TWO_CTA_SMEM) == (cls == 1)) order.push_back(i);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return subs[a].cost > subs[c].cost; });
+        for (size_t i = 0; i < order.size(); i += BATCH_MAX_JOBS) {
+            BatchParams bp;
+            memset(&bp, 0, sizeof(bp));
+            long long item = 0;
+            size_t sm = 0;
+            for (size_t q = i; q < std::min(order.size(), i + BATCH_MAX_JOBS); q++) {
+                const SubJob& sj = subs[order[q]];
+                bp.p[bp.n_jobs] = sj.p;
+                bp.item_begin[bp.n_jobs] = item;
+                item += sj.n_items;
+                sm = std::max(sm, sj.smem);
+                bp.n_jobs++;
+            }
+            bp.item_begin[bp.n_jobs] = item;
+            b->chunks.push_back(bp);
+            b->chunk_smem.push_back(sm);
+            b->n_items_all += item;
+            b->smem = std::max(b->smem, sm);
+        }
     }
     b->total = b->n_items_all;
-    b->smem = smem_max;
     knn_status st;
     if ((st = b->bufs->get(&b->d_head, b->chunks.size())) != KNN_OK) return bail(st);
     if ((st = b->bufs->get(&b->d_err, 1)) != KNN_OK) return bail(st);
@@ -2055,18 +2158,27 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
         cudaError_t e_ = (expr);                                                          \
         if (e_ != cudaSuccess) return bail(fail(KNN_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_))); \
     } while (0)
-    int per_sm = 0;
     b->count = o.stats != nullptr;
-    for (int pass = b->fx ? 0 : 1; pass < 2; pass++) {
-        const BatchKernel kern = batch_kernel(b->dtype, b->count, pass == 0);
-        int ps = 0;
-        BATCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-        BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kern, T, b->smem));
-        per_sm = per_sm ? std::min(per_sm, ps) : ps;
+    for (int pass = b->fx ? 0 : 1; pass < 2; pass++)
+        BATCH_CUDA(cudaFuncSetAttribute(batch_kernel(b->dtype, b->count, pass == 0),
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    int active = 0;
+    for (size_t c = 0; c < b->chunks.size(); c++) {
+        // CTAs per SM that both kernel instances reach with this chunk's layout
+        int per_sm = 0;
+        for (int pass = b->fx ? 0 : 1; pass < 2; pass++) {
+            int ps = 0;
+            BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, batch_kernel(b->dtype, b->count, pass == 0), T,
+                                                                     b->chunk_smem[c]));
+            per_sm = per_sm ? std::min(per_sm, ps) : ps;
+        }
+        if (per_sm < 1) return bail(fail(KNN_EUNSUPPORTED, "the batched kernel does not fit an SM"));
+        const long long items = b->chunks[c].item_begin[b->chunks[c].n_jobs];
+        b->chunk_grid.push_back((int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, items)));
+        b->grid = std::max(b->grid, b->chunk_grid.back());
+        active += items > 0;
     }
-    if (per_sm < 1) return bail(fail(KNN_EUNSUPPORTED, "the batched kernel does not fit an SM"));
-    b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, std::max<int64_t>(1, b->total)));
-    b->launches_per_run = (int)b->chunks.size() * (b->fx ? 2 : 1);
+    b->launches_per_run = active * (b->fx ? 2 : 1);
     BATCH_CUDA(cudaStreamSynchronize(stream));
     tmp.release();
     if (o.use_graph) {
@@ -2106,6 +2218,7 @@ extern "C" knn_status knn_batch_check(const knn_batch* b, void* stream_) {
     unsigned e = 0;
     KNN_CUDA_TRY(cudaMemcpyAsync(&e, b->d_err, sizeof(e), cudaMemcpyDeviceToHost, (cudaStream_t)stream_));
     KNN_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream_));
+    if (e & 2u) return fail(KNN_EINVAL, "a row of a batched job has more features than when the batch was made");
     if (e) return fail(KNN_ETIMEOUT, "a batched work item waited too long for its row's previous group");
     return KNN_OK;
 }

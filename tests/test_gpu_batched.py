@@ -5,6 +5,7 @@ import pytest
 
 from paper_1011_2807_gb300 import synth
 import compare
+from cases import long_row_case
 
 pytestmark = pytest.mark.gpu
 
@@ -150,3 +151,65 @@ def test_bounded_wait_reports_timeout(knn, jobs):
     (bids, bsc), = knn.knn_join_batched([(j["idx"], j["Rd"], j["k"])], blocks_per_group=1)
     torch.cuda.synchronize()
     assert torch.equal(ids, bids) and torch.equal(sc, bsc)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+@pytest.mark.parametrize("bpg", [0, 1])
+def test_batched_long_rows_split(knn, oracle_mod, dtype, bpg):
+    """Jobs whose longest rows need a layout above 110 KB run as two sub-jobs: the rows
+    that fit a layout within 110 KB in a persistent launch at two CTAs per SM (with the
+    jobs that fit it whole), the long rows in a launch of their own.  Results against the
+    oracle (uint8 bit-exact), with one S-block group per row and with one group per S
+    block (rows then wait for their previous group within either launch)."""
+    import torch
+    S, R, Rshort = long_row_case(dtype, 1301)
+    idx = knn.knn_join_build_index(S, block_size=16384)
+    jobs = [(idx, knn.DeviceCSR.from_host(R), 9), (idx, knn.DeviceCSR.from_host(Rshort), 5),
+            (idx, knn.DeviceCSR.from_host(R), 20)]
+    hosts = [R, Rshort, R]
+    b = knn.Batch(jobs, use_graph=True, blocks_per_group=bpg)
+    passes = 2 if dtype == "f32" else 1
+    assert b.info()["kernels_per_launch"] == 2 * passes   # the small-layout launch and the full-layout one
+    outs = b.launch()
+    b.check()
+    torch.cuda.synchronize()
+    for (ix, Rd, k), Rh, (ids, sc) in zip(jobs, hosts, outs):
+        eids, esc, _ = oracle_mod.bf_join(Rh, S, k, threads=8)
+        if dtype == "u8":
+            compare.assert_exact(ids.cpu().numpy(), sc.cpu().numpy(), eids, esc, f"batched long rows k={k}")
+        else:
+            compare.assert_close(Rh, S, list(range(Rh.n_rows)), ids.cpu().numpy(), sc.cpu().numpy(), eids, esc,
+                                 what=f"batched long rows k={k}")
+    b.close()
+    idx.close()
+
+
+def test_batched_row_grown_since_creation(knn):
+    """A batch's layouts are sized for R's row lengths when it is made.  A row that has
+    grown past its layout since is not joined -- the kernel compares the row's length
+    with the layout before it reads a feature of it -- and knn_batch_check reports
+    KNN_EINVAL; with the lengths restored the batch returns the same results again."""
+    import torch
+    from paper_1011_2807_gb300.binding import KNN_EINVAL, KnnError
+    S, R, _ = long_row_case("u8", 1311)
+    idx = knn.knn_join_build_index(S, block_size=16384)
+    Rd = knn.DeviceCSR.from_host(R)
+    b = knn.Batch([(idx, Rd, 5)], use_graph=False, blocks_per_group=1)
+    b.launch()
+    b.check()
+    ref = [t.clone() for t in b.outputs[0]]
+    # rows 30-32 are the long ones, row 33 a short one: moving row 33's start back to row
+    # 32's start empties row 32 and gives row 33 its 2,500 features too
+    assert int(R.indptr[33] - R.indptr[32]) == 2500 and int(R.indptr[34] - R.indptr[33]) < 200
+    Rd.indptr[33] = int(R.indptr[32])
+    b.launch()
+    with pytest.raises(KnnError) as e:
+        b.check()
+    assert e.value.status == KNN_EINVAL
+    Rd.indptr[33] = int(R.indptr[33])
+    b.launch()
+    b.check()
+    torch.cuda.synchronize()
+    assert torch.equal(b.outputs[0][0], ref[0]) and torch.equal(b.outputs[0][1], ref[1])
+    b.close()
+    idx.close()

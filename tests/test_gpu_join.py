@@ -4,6 +4,7 @@ import pytest
 
 from paper_1011_2807_gb300 import synth
 import compare
+from cases import long_row_case, random_u8
 import goldens
 import refdefs
 
@@ -30,17 +31,6 @@ def run(knn, S, R, k, device_r=True, **kw):
     out = (ids.cpu().numpy(), sc.cpu().numpy())
     idx.close()
     return out
-
-
-def random_u8(n, dim, nnz_hi, seed, wmax=100, nnz_lo=0):
-    rng = np.random.default_rng(seed)
-    rows = []
-    for _ in range(n):
-        m = int(rng.integers(nnz_lo, min(nnz_hi, dim) + 1))
-        d = rng.choice(dim, size=m, replace=False)
-        w = rng.integers(1, wmax + 1, size=m)
-        rows.append(list(zip(d.tolist(), w.tolist())))
-    return synth.from_rows(rows, dim, np.uint8)
 
 
 # ----------------------------------------------------------------------------------
@@ -126,33 +116,18 @@ def test_long_rows_run_in_a_launch_of_their_own(knn, oracle_mod, dtype):
     """A few query rows too long for a two-CTA-per-SM shared-memory layout among short
     ones: each S-block launch runs the short rows with the small layout and the long rows
     with the full one.  Results against the oracle (uint8 bit-exact), for S-block-
-    synchronous launches, the fp32 re-join path and one launch over all S blocks."""
+    synchronous launches, IIB, one launch over all S blocks and the fp32 path; the extra
+    launches show that the split ran."""
     import torch
     from paper_1011_2807_gb300.binding import KNN_STATS
-    rng = np.random.default_rng(961)
-    dim = 6000
-    if dtype == "u8":
-        S = random_u8(9000, dim, 80, 962, nnz_lo=10)
-        short = [list(zip(np.sort(rng.choice(dim, int(rng.integers(5, 200)), replace=False)).tolist(),
-                          rng.integers(1, 101, 1000).tolist())) for _ in range(60)]
-        long_ = [list(zip(np.sort(rng.choice(dim, n, replace=False)).tolist(), rng.integers(1, 101, n).tolist()))
-                 for n in (900, 1400, 2500)]
-        rows = short[:30] + long_ + short[30:]
-        R = synth.from_rows([[(d, w) for d, w in r] for r in rows], dim, np.uint8)
-    else:
-        S = synth.zipf_f32(9000, 963, dim=dim, nnz_hi=300)
-        short = [list(zip(np.sort(rng.choice(dim, int(rng.integers(5, 200)), replace=False)).tolist(),
-                          rng.lognormal(0.0, 1.0, 1000).tolist())) for _ in range(60)]
-        long_ = [list(zip(np.sort(rng.choice(dim, n, replace=False)).tolist(), rng.lognormal(0.0, 1.0, n).tolist()))
-                 for n in (1200, 1800, 2500)]
-        rows = short[:30] + long_ + short[30:]
-        R = synth.from_rows(rows, dim, np.float32)
+    S, R, Rshort = long_row_case(dtype, 961)
     k = 9
     eids, esc, _ = oracle_mod.bf_join(R, S, k, threads=8)
-    idx = knn.knn_join_build_index(S, block_size=1024)
-    Rd = knn.DeviceCSR.from_host(R)
+    idx = knn.knn_join_build_index(S, block_size=16384)
+    assert idx.info()["n_blocks"] == 3
+    Rd, Rsd = knn.DeviceCSR.from_host(R), knn.DeviceCSR.from_host(Rshort)
     for kw in (dict(blocks_per_launch=2), dict(blocks_per_launch=2, mode="iib"), dict(blocks_per_launch=100),
-               dict(blocks_per_launch=3, fixed_point=False)):
+               dict(blocks_per_launch=1, fixed_point=False)):
         st = torch.zeros(len(KNN_STATS), dtype=torch.int64, device="cuda")
         ids, sc = knn.knn_join(idx, Rd, k, s_groups=1, stats=st, **kw)
         ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
@@ -161,7 +136,15 @@ def test_long_rows_run_in_a_launch_of_their_own(knn, oracle_mod, dtype):
         else:
             compare.assert_close(R, S, list(range(R.n_rows)), ids, sc, eids, esc, what=f"long rows {kw}")
         w = dict(zip(KNN_STATS, st.cpu().tolist()))
-        assert w["block_steps"] >= R.n_rows * idx.info()["n_blocks"]   # every row, every block
+        assert w["block_steps"] >= R.n_rows * 3   # every row, every block
+    if dtype == "u8":
+        # one launch step: the split adds k_split_rows and the long rows' launch
+        n0 = knn.knn_kernel_launch_count()
+        knn.knn_join(idx, Rsd, k, s_groups=1, blocks_per_launch=100)
+        n1 = knn.knn_kernel_launch_count()
+        knn.knn_join(idx, Rd, k, s_groups=1, blocks_per_launch=100)
+        n2 = knn.knn_kernel_launch_count()
+        assert (n2 - n1) - (n1 - n0) == 2, (n0, n1, n2)
     idx.close()
 
 
