@@ -297,10 +297,11 @@ typedef struct {
  * fp32.                                                                              */
 knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, const knn_batch_opts* opts,
                             void* stream, knn_batch** out);
-/* Runs every job (asynchronously on `stream`): one persistent kernel takes the work
- * items from a counter, in order; a row's group g starts from the top-k its group g-1
- * left (a bounded wait if that item is still running).  Results land in each job's
- * outputs exactly as knn_join would write them.                                     */
+/* Runs every job (asynchronously on `stream`): one persistent kernel per launch class
+ * takes the work items from a counter, in order, round by round (S-block group g of
+ * every job, then group g+1); a row's group g starts from the top-k its group g-1 left
+ * (a bounded wait if that item is still running).  Results land in each job's outputs
+ * exactly as knn_join would write them.                                             */
 knn_status knn_batch_launch(knn_batch* batch, void* stream);
 /* Synchronises `stream` and reports the last run: KNN_EINVAL if a row had more
  * features than when the batch was made, KNN_ETIMEOUT if a work item gave up its

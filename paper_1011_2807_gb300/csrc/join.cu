@@ -761,13 +761,13 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                 li = lo;
             }
             using Mul = typename JT<W>::Mul;
-            // FX: the row accumulates rounded, scaled products in integers (fx_decide)
+            // INT: the row accumulates rounded, scaled products in integers (fx_decide)
             auto scan_items = [&](auto fx_tag, const float fxs) {
-                constexpr bool FX = decltype(fx_tag)::value;
+                constexpr bool INT = decltype(fx_tag)::value;
                 for (uint32_t I = I0; I < I1; I++) {
                     while (ipre[li + 1] <= I) li++;
                     const uint32_t en = lend[li];
-                    const Mul m = JT<W>::scan_mul(FX ? rf_w[li] * fxs : rf_w[li]);
+                    const Mul m = JT<W>::scan_mul(INT ? rf_w[li] * fxs : rf_w[li]);
                     const uint32_t p0 = lbeg[li] + (I - ipre[li]) * (CH * V) + (uint32_t)sl * V;   // this lane's first posting
                     const uint4* src = (const uint4*)(post + p0);
                     uint4 v[U];
@@ -786,7 +786,7 @@ __device__ __forceinline__ void join_row(const JoinParams& p, const int64_t row,
                             for (int j = 0; j < V; j++) {
                                 const bool in = j == 0 || (uint32_t)j < nv;
                                 const uint32_t addr = acc_s + 4u * (uint32_t)JT<W>::post_lid(e[j]);
-                                if constexpr (FX)
+                                if constexpr (INT)
                                     red_add_shared(addr, (int32_t)__float2int_rn(JT<W>::post_val(e[j], in ? m : (Mul)0)));
                                 else
                                     red_add_shared(addr, JT<W>::post_val(e[j], in ? m : (Mul)0));
@@ -1099,54 +1099,141 @@ static JoinKernel join_kernel(knn_dtype dt, bool count, bool bf, bool fx = false
 // ---------------------------------------------------------------------------------
 constexpr int BATCH_MAX_JOBS = 64;   // jobs per launch (their parameters are kernel parameters)
 
+// Work items (job, S-block group g, row) in rounds: round g holds group g of every job
+// that has more than g groups, job by job, row by row.  Jobs are sorted by their group
+// count (descending), so the jobs of a round are a prefix of the list, and the rounds
+// fall into phases of equal prefix: phase h covers rounds [round[h], round[h+1]) with
+// jobs [0, jobs[h]), rows_before[jobs[h]] items per round.
 struct BatchParams {
-    JoinParams p[BATCH_MAX_JOBS];               // each job's join (groups >= 1)
-    long long item_begin[BATCH_MAX_JOBS + 1];   // first work item of each job; items are (group, row)
-    int n_jobs;
+    JoinParams p[BATCH_MAX_JOBS];                // each job's join (groups >= 1), groups descending
+    long long rows_before[BATCH_MAX_JOBS + 1];   // rows of the jobs before this one
+    long long phase_item[BATCH_MAX_JOBS + 1];    // first item of each phase; [n_phases] = all items
+    int phase_round[BATCH_MAX_JOBS + 1];         // first round of each phase
+    int phase_jobs[BATCH_MAX_JOBS];              // jobs in each phase's rounds
+    int n_jobs, n_phases;
 };
 static_assert(sizeof(BatchParams) < 32000, "batch parameters must fit the kernel parameter space");
 
-// Persistent CTAs take work items (job, S-block group, row) from one counter until it
-// runs out; items of one job and group run side by side, so that group's postings stay
-// in L2 while its rows read them, and each row's top-k is carried from group to group.
+// Persistent CTAs take work items from one counter until it runs out.  A round's items
+// of one job run side by side, so that group's postings stay in L2 while its rows read
+// them (for all jobs of the round, when they share an index); each row's top-k is
+// carried from group to group, and a row's next group comes a whole round of rows later.
+// The job, S-block group and row of work item `it` (below the item count) of the round
+// layout: its phase, its round within the phase, its job within the round.
+__device__ __forceinline__ void decode_item(const BatchParams& bp, long long it, int& job, int& g, int64_t& row) {
+    int h = 0, hi = bp.n_phases - 1;
+    while (h < hi) {
+        const int mid = (h + hi + 1) >> 1;
+        if (bp.phase_item[mid] <= it) h = mid;
+        else hi = mid - 1;
+    }
+    const long long per_round = bp.rows_before[bp.phase_jobs[h]];
+    const long long off = it - bp.phase_item[h];
+    const long long rr = off / per_round;
+    g = bp.phase_round[h] + (int)rr;
+    const long long q = off - rr * per_round;   // the item's place in its round
+    int lo = 0;
+    hi = bp.phase_jobs[h] - 1;
+    while (lo < hi) {   // its job: the last one whose rows start at or before q
+        const int mid = (lo + hi + 1) >> 1;
+        if (bp.rows_before[mid] <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    job = lo;
+    const int64_t li = q - bp.rows_before[lo];
+    row = bp.p[lo].row_list ? (int64_t)bp.p[lo].row_list[li] : li;
+}
+
 constexpr long long BATCH_WAIT_SPINS = 1LL << 24;   // default bound: x ~128 ns sleeps, a few seconds
 template <class W, bool COUNT, bool FX>
 __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ BatchParams bp,
                                                        unsigned long long* __restrict__ head,
                                                        unsigned* __restrict__ err, long long wait_spins,
-                                                       int no_publish) {
+                                                       int no_publish, int flagged_only) {
     extern __shared__ __align__(16) unsigned char smem[];
     // the item's job (-1: no items left), S-block group and row, decoded by thread 0
     __shared__ int s_job, s_g, s_row, s_ok;
-    const long long total = bp.item_begin[bp.n_jobs];
+    // flagged_only (the fp32 pass of a float batch, where few rows are flagged): warp 0
+    // claims 32 items at a time and keeps those of flagged rows, taken in order
+    __shared__ long long s_base;
+    __shared__ unsigned s_mask;
+    // otherwise each CTA claims one item ahead (s_next, -1: none yet), so that the claim's
+    // round trip overlaps the loads that start the current item
+    __shared__ long long s_next;
+    // a finished group to announce (s_pub_job >= 0): its row's done counter becomes
+    // s_pub_g + 1 once the next item's first barrier has ordered the CTA's writes of the
+    // carried keys before it
+    __shared__ int s_pub_job, s_pub_g, s_pub_row;
+    const long long total = bp.phase_item[bp.n_phases];
+    if (threadIdx.x == 0) {
+        s_mask = 0u;
+        s_next = -1;
+        s_pub_job = -1;
+    }
     for (;;) {
-        __syncthreads();   // the previous item is finished with shared memory
+        __syncthreads();   // the previous item is finished with shared memory and its outputs
+        if (threadIdx.x == 0 && s_pub_job >= 0) {   // announce it before anything that can wait
+            __threadfence();
+            asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(bp.p[s_pub_job].done + s_pub_row),
+                         "r"(s_pub_g + 1)
+                         : "memory");
+            s_pub_job = -1;
+        }
+        long long it = total;   // thread 0: the item to run
+        unsigned long long ahead = 0;
+        if (flagged_only) {
+            if (threadIdx.x < 32) {
+                const int lane = threadIdx.x;
+                for (;;) {
+                    const unsigned mask = s_mask;
+                    if (mask) {
+                        if (lane == 0) {
+                            it = s_base + (__ffs(mask) - 1);
+                            s_mask = mask & (mask - 1);
+                        }
+                        break;
+                    }
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(head, 32ull);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if ((long long)base >= total) break;
+                    const long long my = (long long)base + lane;
+                    bool fl = false;
+                    if (my < total) {
+                        int mj, mg;
+                        int64_t mr;
+                        decode_item(bp, my, mj, mg, mr);
+                        fl = bp.p[mj].fx_flag[mr] != 0;
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, fl);
+                    if (lane == 0) {
+                        s_base = (long long)base;
+                        s_mask = m;
+                    }
+                    __syncwarp();
+                }
+            }
+        } else if (threadIdx.x == 0) {
+            it = s_next >= 0 ? s_next : (long long)atomicAdd(head, 1ull);
+            // claims stay in order, and a CTA holds at most one item it has not started, larger
+            // than the one it runs: the smallest unfinished item is always running
+            if (it < total) ahead = atomicAdd(head, 1ull);
+        }
         if (threadIdx.x == 0) {
-            const long long it = (long long)atomicAdd(head, 1ull);
             int lo = -1, g = 0, ok = 0;
             int64_t row = 0;
             if (it < total) {
-                lo = 0;
-                int hi = bp.n_jobs - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (bp.item_begin[mid] <= it) lo = mid;
-                    else hi = mid - 1;
-                }
+                decode_item(bp, it, lo, g, row);
                 const JoinParams& J = bp.p[lo];
-                const int64_t local = it - bp.item_begin[lo];
-                const int64_t n_list = (bp.item_begin[lo + 1] - bp.item_begin[lo]) / J.groups;   // rows it covers
-                g = (int)(local / n_list);
-                const int64_t li = local - (int64_t)g * n_list;
-                row = J.row_list ? (int64_t)J.row_list[li] : li;
                 ok = 1;
                 // the fp32 pass after a fixed-point one joins only the rows that pass
                 // flagged: the other rows' items are skipped before any wait (none of them
                 // publishes, and none of them waits)
                 if (!FX && J.fx_flag && !J.fx_flag[row]) ok = 0;
                 // group g continues from group g-1's top-k of this row: that item was taken
-                // earlier (items are handed out in order), so it is running or done; wait
-                // for it with a bounded spin, and give up with an error flag rather than hang
+                // earlier (items are handed out in order -- singly, or in runs of 32 that the
+                // claiming CTA takes in order), so it is running or done; wait for it with a
+                // bounded spin, and give up with an error flag rather than hang
                 if (ok && g > 0) {
                     int* dp = J.done + row;
                     long long spins = 0;
@@ -1175,6 +1262,7 @@ __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ B
             s_g = g;
             s_row = (int)row;
             s_ok = ok;
+            if (!flagged_only) s_next = it < total ? (long long)ahead : total;
         }
         __syncthreads();
         const int job = s_job;
@@ -1190,21 +1278,16 @@ __global__ void __launch_bounds__(1024) k_join_batched(const __grid_constant__ B
             join_row<W, COUNT, false, FX>(J, row, g, g * J.blocks_per_group,
                                           min(J.n_blocks, (g + 1) * J.blocks_per_group), g > 0,
                                           last ? OUT_FINAL : OUT_CARRY, smem);
-        if (!last && !no_publish) {   // publish: the carried keys are in global memory before the flag
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                // the item, re-read: nothing of it needs to stay in registers across the join
-                const int jb = *(volatile int*)&s_job;
-                const int gg = *(volatile int*)&s_g;
-                const int rr = *(volatile int*)&s_row;
-                __threadfence();
-                asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(bp.p[jb].done + rr), "r"(gg + 1) : "memory");
-            }
+        if (!last && !no_publish && threadIdx.x == 0) {   // announced after the next barrier
+            // the item, re-read: nothing of it needs to stay in registers across the join
+            s_pub_job = *(volatile int*)&s_job;
+            s_pub_g = *(volatile int*)&s_g;
+            s_pub_row = *(volatile int*)&s_row;
         }
     }
 }
 
-using BatchKernel = void (*)(const BatchParams, unsigned long long*, unsigned*, long long, int);
+using BatchKernel = void (*)(const BatchParams, unsigned long long*, unsigned*, long long, int, int);
 static BatchKernel batch_kernel(knn_dtype dt, bool count, bool fx = false) {
     if (dt == KNN_U8) return count ? k_join_batched<uint8_t, true, false> : k_join_batched<uint8_t, false, false>;
     if (fx) return count ? k_join_batched<float, true, true> : k_join_batched<float, false, true>;
@@ -1901,9 +1984,9 @@ static knn_status batch_enqueue(const knn_batch* b, cudaStream_t s) {
         const BatchKernel kern = batch_kernel(b->dtype, b->count, pass == 0);
         for (size_t c = 0; c < b->chunks.size(); c++) {
             const BatchParams& bp = b->chunks[c];
-            if (bp.item_begin[bp.n_jobs] == 0) continue;
+            if (bp.phase_item[bp.n_phases] == 0) continue;
             kern<<<b->chunk_grid[c], b->T, b->chunk_smem[c], s>>>(bp, b->d_head + c, b->d_err, b->wait_spins,
-                                                                 b->no_publish);
+                                                                 b->no_publish, b->fx && pass == 1);
             KNN_CUDA_TRY(cudaGetLastError());
         }
     }
@@ -1960,7 +2043,6 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
     Buffers tmp(stream);
     struct JobPlan {
         JoinParams p;
-        int64_t n_items;
         size_t smem;         // shared-memory layout for its longest row
         int r_short = 0;     // > 0: rows up to this length run as a sub-job with a layout within 110 KB
         int rden_short = 0;
@@ -2031,7 +2113,6 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
         p.out_ids = jb.out_ids;
         p.out_scores = jb.out_scores;
         p.stats = (unsigned long long*)o.stats;
-        hj[j].n_items = r.n_rows * groups;
         // larger items first: a row's postings in one group grow with |S| / groups and nnz(r)
         cost[j] = (double)ix->nnz / std::max(1, groups) * (double)(r.nnz + 1) / (double)std::max<int64_t>(1, r.n_rows);
     }
@@ -2096,53 +2177,69 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
     }
     struct SubJob {
         JoinParams p;
-        int64_t n_items;
+        int64_t rows;   // rows its items cover (each in all of its groups)
         size_t smem;
         double cost;
     };
-    std::vector<SubJob> subs;
+    std::vector<SubJob> subs;   // jobs without rows have no items and are left out
     for (int j = 0, q = 0; j < n_jobs; j++) {
         const JobPlan& h = hj[j];
         if (!h.r_short) {
-            subs.push_back({h.p, h.n_items, h.smem, cost[j]});
+            if (h.p.n_rows > 0) subs.push_back({h.p, h.p.n_rows, h.smem, cost[j]});
             continue;
         }
         const int64_t n_short = split_n[2 * q++];
         if (n_short > 0) {
-            SubJob sj{h.p, n_short * h.p.groups, smem_layout(1 << h.p.block_shift, h.r_short, h.rden_short).total,
-                      cost[j]};
+            SubJob sj{h.p, n_short, smem_layout(1 << h.p.block_shift, h.r_short, h.rden_short).total, cost[j]};
             sj.p.row_list = h.lists;
             sj.p.max_r_nnz = h.r_short;
             sj.p.rden_dim = h.rden_short;
             subs.push_back(sj);
         }
         if (n_short < h.p.n_rows) {
-            SubJob sj{h.p, (h.p.n_rows - n_short) * h.p.groups, h.smem, cost[j]};
+            SubJob sj{h.p, h.p.n_rows - n_short, h.smem, cost[j]};
             sj.p.row_list = h.lists + n_short;
             subs.push_back(sj);
         }
     }
     // Chunks: the sub-jobs within TWO_CTA_SMEM, then the others, each class in persistent
-    // launches of up to BATCH_MAX_JOBS sub-jobs, larger items first.
+    // launches of up to BATCH_MAX_JOBS sub-jobs, sorted by group count (descending: the
+    // round layout of BatchParams), larger items first among equal counts.
     for (int cls = 0; cls < 2; cls++) {
         std::vector<int> order;
         for (int i = 0; i < (int)subs.size(); i++)
             if ((subs[i].smem > TWO_CTA_SMEM) == (cls == 1)) order.push_back(i);
-        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return subs[a].cost > subs[c].cost; });
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+            if (subs[a].p.groups != subs[c].p.groups) return subs[a].p.groups > subs[c].p.groups;
+            return subs[a].cost > subs[c].cost;
+        });
         for (size_t i = 0; i < order.size(); i += BATCH_MAX_JOBS) {
             BatchParams bp;
             memset(&bp, 0, sizeof(bp));
-            long long item = 0;
             size_t sm = 0;
             for (size_t q = i; q < std::min(order.size(), i + BATCH_MAX_JOBS); q++) {
                 const SubJob& sj = subs[order[q]];
                 bp.p[bp.n_jobs] = sj.p;
-                bp.item_begin[bp.n_jobs] = item;
-                item += sj.n_items;
+                bp.rows_before[bp.n_jobs + 1] = bp.rows_before[bp.n_jobs] + sj.rows;
                 sm = std::max(sm, sj.smem);
                 bp.n_jobs++;
             }
-            bp.item_begin[bp.n_jobs] = item;
+            // phases: while every job has groups left, all of them; then, as the jobs with
+            // the fewest groups run out, shorter prefixes
+            long long item = 0;
+            int round = 0;
+            for (int a = bp.n_jobs; a >= 1; a--) {
+                const int end_round = bp.p[a - 1].groups;
+                if (end_round <= round) continue;
+                bp.phase_item[bp.n_phases] = item;
+                bp.phase_round[bp.n_phases] = round;
+                bp.phase_jobs[bp.n_phases] = a;
+                bp.n_phases++;
+                item += (long long)(end_round - round) * bp.rows_before[a];
+                round = end_round;
+            }
+            bp.phase_item[bp.n_phases] = item;
+            bp.phase_round[bp.n_phases] = round;
             b->chunks.push_back(bp);
             b->chunk_smem.push_back(sm);
             b->n_items_all += item;
@@ -2151,7 +2248,7 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
     }
     b->total = b->n_items_all;
     knn_status st;
-    if ((st = b->bufs->get(&b->d_head, b->chunks.size())) != KNN_OK) return bail(st);
+    if ((st = b->bufs->get(&b->d_head, std::max<size_t>(1, b->chunks.size()))) != KNN_OK) return bail(st);
     if ((st = b->bufs->get(&b->d_err, 1)) != KNN_OK) return bail(st);
 #define BATCH_CUDA(expr)                                                                  \
     do {                                                                                  \
@@ -2173,7 +2270,7 @@ extern "C" knn_status knn_batch_create(int32_t n_jobs, const knn_job* jobs, cons
             per_sm = per_sm ? std::min(per_sm, ps) : ps;
         }
         if (per_sm < 1) return bail(fail(KNN_EUNSUPPORTED, "the batched kernel does not fit an SM"));
-        const long long items = b->chunks[c].item_begin[b->chunks[c].n_jobs];
+        const long long items = b->chunks[c].phase_item[b->chunks[c].n_phases];
         b->chunk_grid.push_back((int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, items)));
         b->grid = std::max(b->grid, b->chunk_grid.back());
         active += items > 0;

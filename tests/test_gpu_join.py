@@ -381,6 +381,52 @@ def test_float_fixed_point_rejoins_imprecise_rows(knn, oracle_mod):
     idx.close()
 
 
+def test_batched_fp32_pass_takes_only_flagged_rows(knn, oracle_mod):
+    """Rows too imprecise for fixed point (a large weight in a dimension S never uses)
+    interleaved with ordinary rows, in two jobs with one S-block group per block: the
+    batched fp32 pass claims its items in runs of 32 and joins only the flagged rows,
+    every group of them; results within the float tolerance of the oracle, and the work
+    counters show the flagged rows joined twice, as many as the plain join re-joins."""
+    import torch
+    from paper_1011_2807_gb300.binding import KNN_STATS
+    dim = 3001
+    S = synth.zipf_f32(6000, 943, dim=3000, nnz_hi=200)
+    S = synth.CSR(S.indptr, S.indices, S.values, dim)          # dimension 3000 stays empty in S
+    rng = np.random.default_rng(944)
+    rows, flagged = [], []
+    for i in range(150):
+        d = np.sort(rng.choice(3000, 30, replace=False))
+        if rng.random() < 0.2:
+            w = rng.lognormal(0.0, 1.0, 30) * 1e-4
+            rows.append(list(zip(d.tolist(), w.tolist())) + [(3000, 1e4)])   # scores ~1e-5 of |r|
+            flagged.append(i)
+        else:
+            rows.append(list(zip(d.tolist(), rng.lognormal(0.0, 1.0, 30).tolist())))
+    R = synth.from_rows(rows, dim, np.float32)
+    k = 10
+    eids, esc, _ = oracle_mod.bf_join(R, S, k, threads=8)
+    idx = knn.knn_join_build_index(S, block_size=1024)
+    nb = idx.info()["n_blocks"]
+    parts = [(0, 70), (70, 150)]
+    jobs = [(idx, knn.DeviceCSR.from_host(R.slice_rows(a, b)), k) for a, b in parts]
+    st = torch.zeros(len(KNN_STATS), dtype=torch.int64, device="cuda")
+    b = knn.Batch(jobs, blocks_per_group=1, threads=256, use_graph=False, stats=st)
+    b.launch()
+    b.check()
+    ids = np.concatenate([o[0].cpu().numpy() for o in b.outputs])
+    sc = np.concatenate([o[1].cpu().numpy() for o in b.outputs])
+    compare.assert_close(R, S, list(range(R.n_rows)), ids, sc, eids, esc, what="batched, some rows re-joined")
+    w = dict(zip(KNN_STATS, st.cpu().tolist()))
+    assert w["fixed_point_rows"] == R.n_rows * nb, w       # the fixed-point pass: every item
+    n_again = w["block_steps"] // nb - R.n_rows            # rows the fp32 pass joined
+    assert w["block_steps"] % nb == 0 and len(flagged) <= n_again < R.n_rows, (w, len(flagged))
+    sp = torch.zeros(len(KNN_STATS), dtype=torch.int64, device="cuda")
+    knn.knn_join(idx, knn.DeviceCSR.from_host(R), k, s_groups=1, blocks_per_launch=2, stats=sp)
+    assert sp[0].item() == w["block_steps"], (sp.tolist(), w)   # the same rows re-joined
+    b.close()
+    idx.close()
+
+
 @pytest.mark.slow
 def test_config5_shaped_f32_sampled_rows(knn, oracle_mod):
     """The float scale-up's generator (Zipf ids over d = 50,000, power-law nnz up to
