@@ -435,9 +435,9 @@ knn_status knn_threshold_model_params(const knn_model* model, const float** para
  *   - n_rows * k must not exceed (KNN_NOALLOC_SCRATCH_BYTES - 256) / 8 = 2,097,120,
  *     else KNN_EUNSUPPORTED with a message naming the limit.
  * Set-up: the first call on a device (with that device current) looks up the array's
- * device address with cudaGetSymbolAddress and keeps it; make that first call before
- * any stream capture begins.  Every call, the first and the later ones, synchronises
- * `stream`: it reads R's size and longest row back to the host.
+ * device address with cudaGetSymbolAddress and keeps it.  Every call, the first and
+ * the later ones, synchronises `stream`: it reads R's size and longest row back to the
+ * host.
  * All calls share the array and it keeps the last call's contents: calls that overlap
  * on the GPU (other streams or host threads) race on it and must be serialised by the
  * caller.                                                                           */

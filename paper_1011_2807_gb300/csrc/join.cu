@@ -1798,9 +1798,9 @@ extern "C" knn_status knn_merge_topk(int32_t n_parts, const int32_t* const* part
 // Every GPU that loads this library holds that array until the process exits.
 //
 // Set-up: the first call on a device (with that device current) looks up the array's
-// device address with cudaGetSymbolAddress and caches it; make that first call before
-// any stream capture begins.  Every call also synchronises its stream (it reads R's
-// size back and, when validating, R's check record).  All calls share the one array and it keeps
+// device address with cudaGetSymbolAddress and caches it.  Every call also synchronises
+// its stream (it reads R's size back and, when validating, R's check record).  All calls
+// share the one array and it keeps
 // the contents of the last call, so two calls whose work overlaps on the GPU (other
 // streams, other host threads) race on it; the check record is cleared on each call,
 // and every carried key is written before it is read.
