@@ -445,6 +445,81 @@ knn_status knn_join_noalloc(const knn_index* index, const knn_csr* R, int32_t k,
                             const knn_join_opts* opts, int32_t* out_ids, void* out_scores,
                             void* stream);
 
+/* ------------------------------------------------------------------------------ */
+/* MS/MS spectra as sparse vectors (Section 5's preprocessing; host code, no GPU)    */
+/* ------------------------------------------------------------------------------ */
+/* Section 5 makes each spectrum one sparse vector: each peak is a feature, its m/z
+ * times 10 is the dimension index and its intensity the value.  These calls read peak
+ * lists in the MGF or MS2 text formats and build that CSR on the host, ready for
+ * knn_join_build_index (S) or knn_join (R).
+ *   MGF: spectra between "BEGIN IONS" and "END IONS"; KEY=VALUE header lines inside
+ *        (TITLE, PEPMASS, CHARGE, ...) and peak lines "m/z intensity [charge]".
+ *   MS2: "H" header lines, then per spectrum an "S" line, "I"/"Z"/"D" lines and peak
+ *        lines "m/z intensity".
+ * LF or CRLF line ends, space- or tab-separated fields, blank lines and lines starting
+ * with '#', ';' or '!' ignored; numbers as strtod reads them (C locale).  Row i is the
+ * i-th spectrum of the input; a spectrum without kept peaks is an empty row.
+ * Choices the paper leaves open (each settable below):
+ *   - dimension = floor(m/z * mz_scale); a product within 2^-20 below an integer counts
+ *     as that integer (so decimal m/z such as 0.7 lands in the bin its digits name);
+ *   - peaks of one spectrum in the same dimension: the largest intensity, or the sum
+ *     (in file order);
+ *   - peaks with intensity <= min_intensity are dropped (weights must be > 0);
+ *   - weights: the intensity as float32, or uint8 ceil(100 * I / I_max) with I_max the
+ *     spectrum's largest merged intensity (1..100).                                   */
+typedef enum {
+    KNN_SPECTRA_AUTO = 0,   /* MGF if the first line is BEGIN IONS or KEY=VALUE, MS2 if H/S */
+    KNN_SPECTRA_MGF = 1,
+    KNN_SPECTRA_MS2 = 2
+} knn_spectra_format;
+
+typedef enum { KNN_MERGE_MAX = 0, KNN_MERGE_SUM = 1 } knn_spectra_merge;
+typedef enum { KNN_SPECTRA_F32 = 0, KNN_SPECTRA_U8 = 1 } knn_spectra_weights;
+
+typedef struct {
+    knn_spectra_format format;
+    double mz_scale;              /* > 0; 0 = 10 (Section 5)                                  */
+    knn_spectra_merge merge;      /* 0 = largest intensity                                    */
+    knn_spectra_weights weights;  /* 0 = float32 intensities                                  */
+    int32_t dim;                  /* > 0: the vectors' dimension, a peak at or past it is an
+                                     error (give R and S the same dim); 0 = 1 + the largest
+                                     dimension found                                          */
+    double min_intensity;         /* >= 0; peaks with intensity <= it are dropped (0 = keep
+                                     every positive peak)                                     */
+    int64_t chunk_bytes;          /* >= 0; inputs are cut at spectrum starts into chunks of
+                                     about this many bytes that host threads parse side by
+                                     side (0 = 4 MB); the result does not depend on it        */
+} knn_spectra_opts;
+
+typedef struct {
+    int64_t n_spectra;   /* rows                                                               */
+    int64_t n_peaks;     /* peak lines read                                                    */
+    int64_t n_features;  /* features kept (nnz)                                                */
+    int64_t n_dropped;   /* peaks dropped: intensity <= min_intensity (or below float32's
+                            smallest positive value)                                          */
+    int64_t n_merged;    /* peaks merged into another peak's dimension                         */
+    int32_t dim;
+    knn_dtype dtype;
+} knn_spectra_info;
+
+typedef struct knn_spectra knn_spectra;   /* parsed spectra: a host CSR the handle owns  */
+
+/* Parses `len` bytes of MGF or MS2 text.
+ * Errors: KNN_EINVAL (malformed input: the message names the line; a negative or
+ * non-finite m/z, a non-finite intensity, a dimension at or past opts->dim, a bad
+ * option), KNN_EUNSUPPORTED (a dimension past int32, an intensity past float32),
+ * KNN_ENOMEM (host allocation).  On error *out is NULL.                              */
+knn_status knn_spectra_parse(const char* text, size_t len, const knn_spectra_opts* opts,
+                             knn_spectra** out);
+/* Reads the file at `path` and parses it as knn_spectra_parse does (KNN_EINVAL if it
+ * cannot be opened or read).                                                         */
+knn_status knn_spectra_read(const char* path, const knn_spectra_opts* opts, knn_spectra** out);
+/* The spectra as a host CSR (on_device = 0): the arrays belong to `sp` and stay valid
+ * until knn_spectra_free.  dtype KNN_F32 or KNN_U8 as opts->weights asked.            */
+knn_status knn_spectra_csr(const knn_spectra* sp, knn_csr* out);
+knn_status knn_spectra_get_info(const knn_spectra* sp, knn_spectra_info* info);
+void knn_spectra_free(knn_spectra* sp);
+
 #ifdef __cplusplus
 }
 #endif

@@ -664,3 +664,90 @@ def knn_merge_topk(parts, offsets, k: int, stream=None):
     _check(L, L.knn_merge_topk(n, pid, psc, off, int(n_rows), int(k), dtype, out_ids.data_ptr(), out_sc.data_ptr(),
                                _stream_ptr(stream)))
     return out_ids, out_sc
+
+
+# ----------------------------------------------------------------------------------
+# MS/MS spectra as sparse vectors (Section 5's preprocessing; host code, no GPU)
+# ----------------------------------------------------------------------------------
+_SPECTRA_FORMATS = {"auto": 0, "mgf": 1, "ms2": 2}
+_SPECTRA_MERGE = {"max": 0, "sum": 1}
+_SPECTRA_WEIGHTS = {"f32": 0, "u8": 1}
+
+
+class _SpectraOpts(ctypes.Structure):
+    _fields_ = [("format", ctypes.c_int), ("mz_scale", ctypes.c_double), ("merge", ctypes.c_int),
+                ("weights", ctypes.c_int), ("dim", ctypes.c_int32), ("min_intensity", ctypes.c_double),
+                ("chunk_bytes", ctypes.c_int64)]
+
+
+class _SpectraInfo(ctypes.Structure):
+    _fields_ = [("n_spectra", ctypes.c_int64), ("n_peaks", ctypes.c_int64), ("n_features", ctypes.c_int64),
+                ("n_dropped", ctypes.c_int64), ("n_merged", ctypes.c_int64), ("dim", ctypes.c_int32),
+                ("dtype", ctypes.c_int)]
+
+
+def _spectra_lib():
+    L = lib()
+    if not getattr(L, "_spectra_ready", False):
+        P = ctypes.POINTER
+        L.knn_spectra_parse.argtypes = [ctypes.c_char_p, ctypes.c_size_t, P(_SpectraOpts), P(ctypes.c_void_p)]
+        L.knn_spectra_read.argtypes = [ctypes.c_char_p, P(_SpectraOpts), P(ctypes.c_void_p)]
+        L.knn_spectra_csr.argtypes = [ctypes.c_void_p, P(_Csr)]
+        L.knn_spectra_get_info.argtypes = [ctypes.c_void_p, P(_SpectraInfo)]
+        L.knn_spectra_free.argtypes = [ctypes.c_void_p]
+        L.knn_spectra_free.restype = None
+        L._spectra_ready = True
+    return L
+
+
+def _spectra_opts(fmt, mz_scale, merge, weights, dim, min_intensity, chunk_bytes):
+    try:
+        return _SpectraOpts(_SPECTRA_FORMATS[fmt], float(mz_scale), _SPECTRA_MERGE[merge],
+                            _SPECTRA_WEIGHTS[weights], int(dim), float(min_intensity), int(chunk_bytes))
+    except KeyError as e:
+        raise ValueError(f"unknown option value {e}") from None
+
+
+def _spectra_take(L, handle):
+    """Copies the library's host CSR out of `handle` (then freed): (CSR, info dict)."""
+    from .synth import CSR
+    try:
+        c = _Csr()
+        _check(L, L.knn_spectra_csr(handle, ctypes.byref(c)))
+        inf = _SpectraInfo()
+        _check(L, L.knn_spectra_get_info(handle, ctypes.byref(inf)))
+        n, nnz = int(c.n_rows), int(inf.n_features)
+        vdt = np.uint8 if c.dtype == KNN_U8 else np.float32
+
+        def take(ptr, count, dt):
+            if count == 0 or not ptr:
+                return np.zeros(count, dt)
+            return np.frombuffer((ctypes.c_char * (count * np.dtype(dt).itemsize)).from_address(ptr), dt).copy()
+
+        csr = CSR(take(c.indptr, n + 1, np.int64), take(c.indices, nnz, np.int32), take(c.values, nnz, vdt),
+                  int(c.dim))
+        info = {f: getattr(inf, f) for f, _ in _SpectraInfo._fields_}
+        return csr, info
+    finally:
+        L.knn_spectra_free(handle)
+
+
+def spectra_parse(text, *, fmt: str = "auto", mz_scale: float = 10.0, merge: str = "max", weights: str = "f32",
+                  dim: int = 0, min_intensity: float = 0.0, chunk_bytes: int = 0):
+    """knn_spectra_parse: MGF or MS2 text (str or bytes) -> (CSR on the host, info dict)."""
+    L = _spectra_lib()
+    data = text.encode() if isinstance(text, str) else bytes(text)
+    o = _spectra_opts(fmt, mz_scale, merge, weights, dim, min_intensity, chunk_bytes)
+    h = ctypes.c_void_p()
+    _check(L, L.knn_spectra_parse(data, len(data), ctypes.byref(o), ctypes.byref(h)))
+    return _spectra_take(L, h.value)
+
+
+def spectra_read(path, *, fmt: str = "auto", mz_scale: float = 10.0, merge: str = "max", weights: str = "f32",
+                 dim: int = 0, min_intensity: float = 0.0, chunk_bytes: int = 0):
+    """knn_spectra_read: an MGF or MS2 file -> (CSR on the host, info dict)."""
+    L = _spectra_lib()
+    o = _spectra_opts(fmt, mz_scale, merge, weights, dim, min_intensity, chunk_bytes)
+    h = ctypes.c_void_p()
+    _check(L, L.knn_spectra_read(os.fsencode(path), ctypes.byref(o), ctypes.byref(h)))
+    return _spectra_take(L, h.value)

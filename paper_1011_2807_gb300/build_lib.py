@@ -1,6 +1,7 @@
 """Builds libknnjoin.so (the CUDA library behind include/knn_join.h) in-tree.
 
-Each ``csrc/*.cu`` translation unit is compiled for sm_103a in parallel, then linked
+Each ``csrc/*.cu`` translation unit is compiled for sm_103a in parallel (``csrc/*.cpp``,
+host code, by nvcc's host compiler), then linked
 into ``paper_1011_2807_gb300/libknnjoin.so`` against the shared CUDA runtime (so the
 process shares one runtime with PyTorch).  Objects go to ``paper_1011_2807_gb300/_build``.
 """
@@ -38,7 +39,7 @@ def _stale(lib: str, deps: list[str]) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    srcs = sorted(glob.glob(os.path.join(SRC, "*.cu")))
+    srcs = sorted(glob.glob(os.path.join(SRC, "*.cu")) + glob.glob(os.path.join(SRC, "*.cpp")))
     deps = srcs + glob.glob(os.path.join(SRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
     if not force and not _stale(LIB, deps):
         return LIB
@@ -47,7 +48,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     flags = FLAGS + (extra_flags or [])
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(OUT, os.path.splitext(os.path.basename(src))[0] + ".o")
         cmd = [cc, *ARCH, *flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

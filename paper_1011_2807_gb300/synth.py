@@ -309,6 +309,54 @@ def spectrum_u8(n: int, seed: int, *, role: str = "S", dim: int = 10000,
     return CSR(indptr, idx, vals, dim)
 
 
+def spectra_text(n: int, seed: int, *, fmt: str = "mgf", peaks_lo: int = 20, peaks_hi: int = 600,
+                 mz_max: float = 999.9, noise: bool = True) -> str:
+    """MS/MS peak lists as MGF or MS2 text: n spectra, peak counts log-normal (mean
+    ~150, clipped to [peaks_lo, peaks_hi]), m/z around the spectrum-shaped workload's
+    mixture centres (dimension / 10, 4 decimals), log-normal intensities.  With
+    ``noise`` the text also carries what real files do: CRLF and tab-separated lines,
+    comments, header records, a charge field after some MGF peaks, intensities in
+    scientific notation, zero or negative intensities, and peaks closer than 0.1 in
+    m/z (two peaks in one dimension)."""
+    rng = np.random.default_rng(seed)
+    centres = mixture_centres(config_seed(2, "mix")) / 10.0
+    counts = np.clip(np.rint(rng.lognormal(4.835, 0.6, size=n)), peaks_lo, peaks_hi).astype(np.int64)
+    out = []
+    nl = "\n"
+    if fmt == "ms2":
+        out.append("H\tCreationDate\tsynthetic" + nl + "H\tExtractor\tsynth.spectra_text" + nl)
+    for i in range(n):
+        m = int(counts[i])
+        mz = centres[rng.integers(0, len(centres), size=m)] + 20.0 * rng.standard_normal(size=m)
+        mz = np.clip(mz, 0.0, mz_max)
+        if noise and m > 2:   # a few peaks within 0.1 of another
+            k = max(1, m // 20)
+            src = rng.integers(0, m, size=k)
+            mz[rng.integers(0, m, size=k)] = np.clip(mz[src] + rng.uniform(-0.04, 0.04, size=k), 0.0, mz_max)
+        inten = rng.lognormal(6.0, 1.5, size=m)
+        if noise:
+            bad = rng.random(size=m) < 0.02
+            inten[bad] = rng.choice([0.0, -1.0], size=int(bad.sum()))
+        eol = "\r\n" if noise and rng.random() < 0.3 else nl
+        if fmt == "mgf":
+            out.append("BEGIN IONS" + eol + f"TITLE=synthetic spectrum {i}" + eol +
+                       f"PEPMASS={rng.uniform(300, 1500):.4f}" + eol + f"CHARGE={int(rng.integers(1, 4))}+" + eol)
+        else:
+            out.append(f"S\t{i + 1:06d}\t{i + 1:06d}\t{rng.uniform(300, 1500):.4f}" + eol +
+                       f"Z\t{int(rng.integers(1, 4))}\t{rng.uniform(600, 3000):.4f}" + eol)
+        for j in range(m):
+            style = int(rng.integers(0, 4)) if noise else 0
+            w = f"{inten[j]:.2f}" if style != 1 else f"{inten[j]:.6e}"
+            sep = "\t" if style == 2 else " "
+            extra = " 1+" if (fmt == "mgf" and style == 3) else ""
+            out.append(f"{mz[j]:.4f}{sep}{w}{extra}{eol}")
+            if noise and rng.random() < 0.005:
+                out.append("# a comment line" + eol)
+        if fmt == "mgf":
+            out.append("END IONS" + eol + (eol if noise and rng.random() < 0.5 else ""))
+    return "".join(out)
+
+
 def powerlaw_nnz(rng, n: int, lo: int = 5, hi: int = 2000, a: float = 1.67) -> np.ndarray:
     support = np.arange(lo, hi + 1, dtype=np.float64)
     p = support ** (-a)
